@@ -1,0 +1,314 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 MRRR tridiagonal eigensolver (FP64).
+
+Workload (one "step"): all eigenpairs of the two clustered-spectrum
+tridiagonals of n ~ 20,000 -- the Wilkinson matrix W+ (d_i = |i-(n+1)/2|,
+e_i = 1, n = 20001) and 952 copies of W21+ glued by e = 1e-10 (n = 19,992) --
+solved one after the other through the library (Sec. 2.3 of the paper names
+both test families).  Metric: eigenpairs per second, whole job.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle
+(bisection + inverse iteration, plain C) on a bounded sample of the same
+workload on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1205_2107_gb300 import inputs  # noqa: E402
+
+METRIC = "FP64 tridiagonal eigenpairs/s + roofline fraction; batched & adjoint vs plain"
+UNIT = "eigenpairs/s"
+WORKLOAD = "clustered spectra n~20000: Wilkinson W+ n=20001 + glued W21+ x952 (n=19992, glue 1e-10), all eigenpairs"
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070  # SMs x DFMA/clk/SM x flops/DFMA x GHz (max SM clock)
+# Algorithmic FP64 flops per eigenvalue and matrix row for each stage (model
+# fixed in the design notes): bisection 4 flops per row and Sturm step with
+# B = 32 steps; twisted factorization, solve and normalisation 15 per row.
+STAGE_FLOPS_PER_ROW = {"bisect_root": 4 * 32, "prerefine": 4 * 32, "refine": 4 * 32, "vectors": 15}
+
+
+def workload_matrices():
+    d1, e1 = inputs.wilkinson_plus(20001)
+    d2, e2 = inputs.glued_wilkinson(952)
+    return [("wilkinson_plus_20001", d1, e1), ("glued_w21_x952", d2, e2)]
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = max(smax, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() in ("active", "1"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle leg (reference arm and cpu_baseline)
+
+def oracle_sample(mats, per_matrix: int, nthreads: int, offset: int = 0):
+    """Eigenpairs of a sample of indices of each matrix by the oracle
+    (bisection on T for lambda_j, inverse iteration for z_j).  Returns
+    (eigenpairs, seconds)."""
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+    oracle.build()
+    jobs = []
+    for _, d, e in mats:
+        n = len(d)
+        idx = np.linspace(1, n, per_matrix).astype(int)
+        idx = np.clip(idx + offset, 1, n)
+        jobs += [(d, e, int(j)) for j in idx]
+
+    def one(job):
+        d, e, j = job
+        lam = oracle.kth_eigenvalue(d, e, j)
+        oracle.cluster_vectors(d, e, [lam])
+        return 1
+
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=nthreads) as ex:
+        done = sum(ex.map(one, jobs))
+    return done, time.perf_counter() - t0
+
+
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return
+    import oracle
+    mats = workload_matrices()
+    cores = oracle.num_threads(0)
+    per = args.ref_sample
+    for w in range(args.warmup):
+        oracle_sample(mats, max(per // 4, 2), cores, offset=w)
+    total_pairs, total_t = 0, 0.0
+    for s in range(args.steps):
+        p, t = oracle_sample(mats, per, cores, offset=s + 1)
+        total_pairs += p
+        total_t += t
+    value = total_pairs / total_t
+    sample = (f"{per} eigenpairs per matrix per step (evenly spaced indices), oracle bisection on T + "
+              f"inverse iteration, {cores} threads")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU leg
+
+def run_ours(args, rank: int, world: int):
+    import torch
+    import torch.distributed as dist
+    from paper_1205_2107_gb300 import api, build
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    mats = workload_matrices()
+    dmats = [(nm, torch.tensor(d, device=dev), torch.tensor(np.append(e, 0.0), device=dev))
+             for nm, d, e in mats]
+    pairs_per_step = sum(len(d) for _, d, _ in mats)
+    plans = [api.Plan(local) for _ in mats]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(check: bool):
+        out = []
+        for (nm, d, e), plan in zip(dmats, plans):
+            out.append(api.eigh_tridiagonal(d, e, plan=plan, check=check))
+        return out
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(max(args.warmup, 3) if args.warmup > 0 else 0):
+        step(check=True)
+    for plan in plans:
+        plan.set_timing(True)
+    barrier()
+    times = []
+    stage_ms: dict[str, float] = {}
+    launches = 0
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize(dev)
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            res = step(check=False)
+            ev1.record(stream)
+            ev1.synchronize()
+            times.append(ev0.elapsed_time(ev1))
+            for plan in plans:
+                prof = plan.profile()
+                launches += prof["launches"]
+                for k, v in prof["stages"].items():
+                    stage_ms[k] = stage_ms.get(k, 0.0) + v
+    barrier()
+    for plan in plans:
+        info = plan.info()
+        if info["status"] != 0:
+            raise SystemExit(f"solver reported status {info['status']} ({info})")
+        plan.set_timing(False)
+    total_ms = sum(times)
+    tmax = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    total_ms = float(tmax.item())
+    value = world * pairs_per_step * args.steps / (total_ms * 1e-3)
+
+    # end to end through the public API with host buffers
+    hostd = [(torch.tensor(d).pin_memory(), torch.tensor(np.append(e, 0.0)).pin_memory()) for _, d, e in mats]
+    h2d = sum(a.numel() * 8 + b.numel() * 8 for a, b in hostd)
+    d2h = pairs_per_step * 8
+    for _ in range(2):
+        for (hd, he), plan in zip(hostd, plans):
+            W, Z = api.eigh_tridiagonal(hd.to(dev, non_blocking=True), he.to(dev, non_blocking=True), plan=plan)
+            W.cpu()
+    barrier()
+    e2e_times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for (hd, he), plan in zip(hostd, plans):
+            W, Z = api.eigh_tridiagonal(hd.to(dev, non_blocking=True), he.to(dev, non_blocking=True), plan=plan,
+                                        check=False)
+            W.cpu()
+        torch.cuda.synchronize(dev)
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_value = world * pairs_per_step * args.steps / sum(e2e_times)
+
+    # roofline of the dominant stage
+    dom = max(stage_ms, key=stage_ms.get) if stage_ms else None
+    roof = None
+    if dom:
+        per_launch_ms = stage_ms[dom] / args.steps / len(mats)
+        rows = sum(len(d) * len(d) for _, d, _ in mats) / len(mats)  # eigenvalues x rows per solve
+        flops = STAGE_FLOPS_PER_ROW.get(dom, 4 * 32) * rows
+        achieved = flops / (per_launch_ms * 1e-3) / 1e9
+        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None,
+                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz"}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        cores = oracle.num_threads(0)
+        per = args.ref_sample
+        oracle_sample(mats, 4, cores)
+        p, t = oracle_sample(mats, per, cores, offset=1)
+        cpu = {"value": p / t, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{per} eigenpairs per matrix (evenly spaced indices) of the same two matrices: "
+                         f"oracle bisection on T + inverse iteration, {t:.1f} s"}
+    clocks = clk.summary()
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": [len(d) for _, d, _ in mats],
+                       "eigenpairs_per_step": pairs_per_step,
+                       "l2": "flushed before each step (256 MB write); Z output 3.2 GB per matrix",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "clocks": clocks, "gpu_launches": launches,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "roofline": roof, "cpu_baseline": cpu,
+            "stages_ms_per_step": {k: v / args.steps for k, v in sorted(stage_ms.items())}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--ref-sample", type=int, default=48, help="oracle eigenpairs per matrix per step")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

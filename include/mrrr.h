@@ -1,0 +1,209 @@
+/*
+ * mrrr.h -- C ABI of a single-GPU (NVIDIA GB300, sm_103a) FP64 MRRR solver
+ * for the real symmetric tridiagonal eigenproblem  T z = lambda z.
+ *
+ * The method is the MRRR algorithm as summarised in Petschow, Peise and
+ * Bientinesi, "High-performance solvers for dense Hermitian eigenproblems"
+ * (arXiv:1205.2107), Sec. 3.1.1 "The MRRR algorithm": a root representation
+ * L0 D0 L0^T = T - sigma I, bisection for eigenvalue approximations,
+ * classification into singletons and clusters by relative gap (tol 1e-3),
+ * child representations Lc Dc Lc^T = L0 D0 L0^T - sigma_c I for clusters,
+ * recursion, and eigenvectors by one step of inverse iteration with a
+ * twisted factorization (Eq. errorangle).  The problem statement -- all or an
+ * index subset il..iu of the eigenpairs -- is the paper's (Sec. 1.1,
+ * Sec. 2.3, Sec. 5).  The accuracy goals are Eqs. Tresnorm / Torthogo
+ * (Sec. 2.3).  Batched solves and the backward (adjoint) pass are not in the
+ * paper; they reuse the same representation of the problem.
+ *
+ * Conventions for every entry point:
+ *   - all array arguments are DEVICE pointers unless stated otherwise;
+ *   - the caller owns every buffer: inputs, outputs and the workspace; the
+ *     library never allocates device memory on the solve path;
+ *   - work is enqueued on the given stream; most calls return before the GPU
+ *     has finished (see each call);
+ *   - no exception crosses the ABI; each call returns an mrrr_status.  Errors
+ *     that only the GPU can detect (non-finite input, non-convergence, a full
+ *     node pool) are recorded in a device status word that mrrr_get_status()
+ *     returns;
+ *   - indices il, iu are 1-based and inclusive over the whole T (across split
+ *     blocks); W comes out ascending and Z column-major, column j belonging
+ *     to W[j]; the sign of each column makes its twist entry positive.
+ */
+#ifndef MRRR_H
+#define MRRR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A CUDA stream (cudaStream_t); NULL is the legacy default stream. */
+typedef void* mrrr_stream;
+
+typedef enum mrrr_status {
+  MRRR_OK = 0,
+  MRRR_ERR_ARG = 1,        /* invalid argument (size, range, null pointer) */
+  MRRR_ERR_WORKSPACE = 2,  /* workspace missing or smaller than required   */
+  MRRR_ERR_NONFINITE = 3,  /* d or e holds NaN or Inf (found on the GPU)   */
+  MRRR_ERR_NOCONV = 4,     /* an iteration hit its cap (bisection, RQI)    */
+  MRRR_ERR_QUEUE = 5,      /* cluster-node table or representation pool full */
+  MRRR_ERR_TIMEOUT = 6,    /* a bounded device wait gave up                */
+  MRRR_ERR_CUDA = 7,       /* a CUDA runtime call failed                   */
+  MRRR_ERR_NOTIMPL = 8     /* option combination not implemented           */
+} mrrr_status;
+
+/* Tunables.  Zero-initialise and call mrrr_options_default(); fields left at
+   0 keep their defaults. */
+typedef struct mrrr_options {
+  double gap_tol;          /* singleton threshold on the relative gap (1e-3, Sec. 3.1.1) */
+  double classify_rtol;    /* relative interval width reached by bisection before
+                              classification (2^-20) */
+  int max_depth;           /* cluster-tree depth limit (64); deeper clusters take the
+                              documented fallback and are counted in mrrr_info */
+  int max_bisect_steps;    /* per interval and pass (256) */
+  int max_rq_iters;        /* Rayleigh-quotient iterations per eigenvector (12) */
+  int threads_per_block;   /* CUDA block size of the interval kernels (128) */
+  int vec_blocks_per_sm;   /* resident blocks per SM of the eigenvector kernel (4) */
+  int reserved0;
+  int64_t max_nodes;       /* capacity of the cluster-node table (0 = automatic) */
+  int64_t pool_rows;       /* capacity of the child-representation pool in rows of
+                              32 bytes (0 = automatic) */
+  double cluster_rtol;     /* relative interval width of cluster eigenvalues before a
+                              child shift is placed, and of their refinement in the
+                              child (2^-40) */
+  double root_perturb;     /* relative size, in units of eps, of the seeded random
+                              perturbation of each root representation entry (4) */
+} mrrr_options;
+
+/* Counters reported by mrrr_get_status (device values after the last solve). */
+typedef struct mrrr_info {
+  int status;              /* device status word (an mrrr_status)           */
+  int depth;               /* deepest cluster level reached                 */
+  int64_t nodes;           /* cluster nodes created (roots excluded)        */
+  int64_t pool_rows_used;  /* child-representation rows needed              */
+  int64_t fallbacks;       /* eigenvalues that took the depth/shift fallback */
+  int64_t rq_iters;        /* Rayleigh-quotient iterations, all vectors     */
+  int64_t levels;          /* cluster levels processed                      */
+  int64_t diag[8];         /* event counters: [0] root-shift retries exhausted,
+                              [1] root bisection cap, [2] child bracket not
+                              confirmed, [3] child bisection cap, [4] RQ
+                              iteration cap, [5] child growth bound missed,
+                              [6] depth-limit fallbacks, [7] capacity fallbacks */
+} mrrr_info;
+
+typedef struct mrrr_plan mrrr_plan;
+
+/* Fill *opt with the defaults above.  Never fails for a non-NULL opt. */
+mrrr_status mrrr_options_default(mrrr_options* opt);
+
+/* Create a plan on the current CUDA device.  opt may be NULL (defaults).
+   The plan owns a small pinned host buffer and its CUDA graphs; it is not
+   thread-safe: use one plan per host thread. */
+mrrr_status mrrr_plan_create(mrrr_plan** plan, const mrrr_options* opt);
+mrrr_status mrrr_plan_destroy(mrrr_plan* plan);
+
+/* Bytes of device workspace a solve needs.  batch problems whose sizes sum
+   to n_total, largest n_max, requesting k_total eigenpairs in all.  The
+   figure holds the automatic node and pool capacities unless the options
+   set them.  Host-only; never fails for valid sizes. */
+mrrr_status mrrr_workspace_size(const mrrr_plan* plan, int batch, int64_t n_total, int64_t k_total,
+                                int n_max, size_t* bytes);
+
+/*
+ * mrrr_stein: eigenpairs il..iu of one symmetric tridiagonal T (paper
+ * Sec. 3.1.1; subset at O(nk) cost, Sec. 2.3).
+ *   n          order of T (n >= 0; n = 0 is a no-op)
+ *   d, e       device, d[n] diagonal, e[n-1] off-diagonal (read only)
+ *   il, iu     1-based inclusive range, 1 <= il <= iu <= n
+ *   W          device, W[iu-il+1] eigenvalues, ascending
+ *   Z          device, column-major n x (iu-il+1) with leading dimension
+ *              ldz >= n; may be NULL for eigenvalues only
+ *   workspace  device, ws_bytes >= mrrr_workspace_size(plan, 1, n, k, n)
+ *   stream     CUDA stream for every launch
+ * Returns MRRR_ERR_ARG / MRRR_ERR_WORKSPACE for bad host-side arguments.
+ * The call synchronises the stream once per cluster level; device-side
+ * errors are read with mrrr_get_status.
+ */
+mrrr_status mrrr_stein(mrrr_plan* plan, int n, const double* d, const double* e, int il, int iu,
+                       double* W, double* Z, int64_t ldz, void* workspace, size_t ws_bytes,
+                       mrrr_stream stream);
+
+/*
+ * mrrr_stein_batched: many independent problems in one set of launches.
+ *   batch      number of problems
+ *   d_off      device int64[batch+1]; problem p owns rows d_off[p]..d_off[p+1]-1
+ *   d, e       device packed arrays of d_off[batch] doubles; e uses the same
+ *              offsets (the last entry of each problem is ignored)
+ *   il, iu     device int32[batch] or NULL (NULL = all eigenpairs)
+ *   W, w_off   device; problem p writes W[w_off[p] .. w_off[p]+k_p-1]
+ *   Z, z_off   device (Z may be NULL); problem p writes an n_p x k_p
+ *              column-major block at Z + z_off[p] with leading dimension n_p
+ *   n_max      largest n_p; k_total = sum of k_p (workspace sizing)
+ * Argument ranges inside the device arrays are checked on the GPU
+ * (MRRR_ERR_ARG in the status word).
+ */
+mrrr_status mrrr_stein_batched(mrrr_plan* plan, int batch, const int64_t* d_off, const double* d,
+                               const double* e, const int* il, const int* iu, double* W,
+                               const int64_t* w_off, double* Z, const int64_t* z_off, int64_t n_total,
+                               int64_t k_total, int n_max, void* workspace, size_t ws_bytes,
+                               mrrr_stream stream);
+
+/*
+ * mrrr_backward: gradient of a scalar loss L(W, Z) with respect to (d, e)
+ * for a batch of problems solved for ALL eigenpairs, given Wbar = dL/dW and
+ * Zbar = dL/dZ (either may be NULL).  Not in the paper: first-order
+ * perturbation theory of T = Z diag(W) Z^T,
+ *   dbar_j = sum_i Wbar_i Z(j,i)^2 + M(j,j),
+ *   ebar_j = 2 sum_i Wbar_i Z(j,i) Z(j+1,i) + M(j,j+1) + M(j+1,j),
+ *   M = Z (F o (Z^T Zbar)) Z^T,  F(i,j) = 1/(W_j - W_i) if |W_j - W_i| > tau,
+ *   tau = tau_rel * max|W| of the problem; F(i,j) = 0 otherwise.
+ *   d_off      device int64[batch+1] as in mrrr_stein_batched (Z is n_p x n_p
+ *              at z offset sum_{q<p} n_q^2, W at d_off[p])
+ *   dbar, ebar device outputs with the packing of d and e (ebar's last entry
+ *              of each problem is written as 0)
+ */
+mrrr_status mrrr_backward(mrrr_plan* plan, int batch, const int64_t* d_off, const double* W,
+                          const double* Z, const double* Wbar, const double* Zbar, double tau_rel,
+                          int n_max, double* dbar, double* ebar, void* workspace, size_t ws_bytes,
+                          mrrr_stream stream);
+
+/* Bytes of workspace mrrr_backward needs for batch problems of order <= n_max. */
+mrrr_status mrrr_backward_workspace_size(const mrrr_plan* plan, int batch, int n_max, size_t* bytes);
+
+/* Stage profile of the last solve on a plan.  launches counts the kernels
+   the solve enqueued; when timing is enabled (mrrr_set_timing) the solve
+   records CUDA events between its stages on its stream and ms[i] holds the
+   time of stage name[i] summed over cluster levels.  Not in the paper:
+   measurement support. */
+typedef struct mrrr_profile {
+  int64_t launches;
+  int nstages;
+  int pad_;
+  char name[32][24];
+  double ms[32];
+} mrrr_profile;
+
+/* Enable (1) or disable (0) per-stage event timing on a plan.  Timing adds
+   one event record per stage and a final event synchronisation. */
+mrrr_status mrrr_set_timing(mrrr_plan* plan, int enable);
+
+/* Copy the profile of the last solve on the plan into *out. */
+mrrr_status mrrr_get_profile(const mrrr_plan* plan, mrrr_profile* out);
+
+/* Synchronise stream and report the device status word and counters of the
+   last solve on this plan.  out may be NULL.  Returns info.status. */
+mrrr_status mrrr_get_status(mrrr_plan* plan, mrrr_stream stream, mrrr_info* out);
+
+/* Static English text for a status code. */
+const char* mrrr_status_string(mrrr_status s);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int mrrr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MRRR_H */

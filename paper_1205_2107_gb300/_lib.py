@@ -1,0 +1,106 @@
+"""ctypes binding of the C ABI in include/mrrr.h (argument marshalling only).
+
+The shared library libmrrr.so is built in-tree by ``build.build()``.  Loading
+fails loudly when it is missing: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+c_double, c_int, c_int64, c_size_t, c_void_p = (ctypes.c_double, ctypes.c_int, ctypes.c_int64,
+                                               ctypes.c_size_t, ctypes.c_void_p)
+
+STATUS = {0: "MRRR_OK", 1: "MRRR_ERR_ARG", 2: "MRRR_ERR_WORKSPACE", 3: "MRRR_ERR_NONFINITE",
+          4: "MRRR_ERR_NOCONV", 5: "MRRR_ERR_QUEUE", 6: "MRRR_ERR_TIMEOUT", 7: "MRRR_ERR_CUDA",
+          8: "MRRR_ERR_NOTIMPL"}
+OK, ERR_ARG, ERR_WORKSPACE, ERR_NONFINITE, ERR_NOCONV, ERR_QUEUE, ERR_TIMEOUT, ERR_CUDA, ERR_NOTIMPL = range(9)
+
+# every function include/mrrr.h declares
+EXPORTS = ["mrrr_options_default", "mrrr_plan_create", "mrrr_plan_destroy", "mrrr_workspace_size",
+           "mrrr_stein", "mrrr_stein_batched", "mrrr_backward", "mrrr_backward_workspace_size",
+           "mrrr_get_status", "mrrr_status_string", "mrrr_version", "mrrr_set_timing", "mrrr_get_profile"]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("gap_tol", c_double), ("classify_rtol", c_double), ("max_depth", c_int),
+                ("max_bisect_steps", c_int), ("max_rq_iters", c_int), ("threads_per_block", c_int),
+                ("vec_blocks_per_sm", c_int), ("reserved0", c_int), ("max_nodes", c_int64),
+                ("pool_rows", c_int64), ("cluster_rtol", c_double), ("root_perturb", c_double)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("status", c_int), ("depth", c_int), ("nodes", c_int64), ("pool_rows_used", c_int64),
+                ("fallbacks", c_int64), ("rq_iters", c_int64), ("levels", c_int64), ("diag", c_int64 * 8)]
+
+    def as_dict(self) -> dict:
+        out = {f: getattr(self, f) for f, _ in self._fields_ if f != "diag"}
+        out["diag"] = list(self.diag)
+        return out
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("launches", c_int64), ("nstages", c_int), ("pad_", c_int), ("name", (ctypes.c_char * 24) * 32),
+                ("ms", c_double * 32)]
+
+    def stages(self) -> dict:
+        return {bytes(self.name[i]).split(b"\0")[0].decode(): float(self.ms[i]) for i in range(self.nstages)}
+
+
+class MrrrError(RuntimeError):
+    def __init__(self, code: int, where: str = ""):
+        self.code = int(code)
+        super().__init__(f"{where}: {STATUS.get(self.code, self.code)}")
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libmrrr.so (optionally building it first)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build_if_missing:
+            _build.build()
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library not built: {path} is missing (call build())")
+        lib = ctypes.CDLL(path)
+        P = c_void_p
+        dp = c_void_p
+        lib.mrrr_options_default.argtypes = [ctypes.POINTER(Options)]
+        lib.mrrr_plan_create.argtypes = [ctypes.POINTER(c_void_p), ctypes.POINTER(Options)]
+        lib.mrrr_plan_destroy.argtypes = [P]
+        lib.mrrr_workspace_size.argtypes = [P, c_int, c_int64, c_int64, c_int, ctypes.POINTER(c_size_t)]
+        lib.mrrr_stein.argtypes = [P, c_int, dp, dp, c_int, c_int, dp, dp, c_int64, dp, c_size_t, P]
+        lib.mrrr_stein_batched.argtypes = [P, c_int, dp, dp, dp, dp, dp, dp, dp, dp, dp, c_int64, c_int64,
+                                           c_int, dp, c_size_t, P]
+        lib.mrrr_backward.argtypes = [P, c_int, dp, dp, dp, dp, dp, c_double, c_int, dp, dp, dp, c_size_t, P]
+        lib.mrrr_backward_workspace_size.argtypes = [P, c_int, c_int, ctypes.POINTER(c_size_t)]
+        lib.mrrr_get_status.argtypes = [P, P, ctypes.POINTER(Info)]
+        lib.mrrr_status_string.argtypes = [c_int]
+        lib.mrrr_status_string.restype = ctypes.c_char_p
+        lib.mrrr_version.argtypes = []
+        lib.mrrr_set_timing.argtypes = [P, c_int]
+        lib.mrrr_get_profile.argtypes = [P, ctypes.POINTER(Profile)]
+        for name in EXPORTS:
+            if name not in ("mrrr_status_string", "mrrr_version"):
+                getattr(lib, name).restype = c_int
+        lib.mrrr_version.restype = c_int
+        _lib = lib
+        return lib
+
+
+def check(rc: int, where: str) -> None:
+    if rc != OK:
+        raise MrrrError(rc, where)

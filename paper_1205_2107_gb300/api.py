@@ -1,0 +1,269 @@
+"""Python API over the C ABI: plans, workspaces and the solver calls.
+
+PyTorch supplies device memory and the current CUDA stream; every step of the
+solve runs in the CUDA library (libmrrr.so).  Inputs must be float64 CUDA
+tensors; there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib
+
+_F64 = torch.float64
+
+
+def _stream_handle(device: torch.device) -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _ptr(t: torch.Tensor | None) -> ctypes.c_void_p:
+    return ctypes.c_void_p(t.data_ptr() if t is not None else None)
+
+
+def _check_input(x: torch.Tensor, name: str) -> torch.Tensor:
+    if not isinstance(x, torch.Tensor) or not x.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if x.dtype != _F64:
+        raise TypeError(f"{name} must be float64")
+    return x.contiguous()
+
+
+class Plan:
+    """A solver plan (options + reusable device workspace) on one GPU.
+
+    Options are the fields of ``mrrr_options`` (gap_tol, classify_rtol,
+    max_depth, max_bisect_steps, max_rq_iters, threads_per_block,
+    vec_blocks_per_sm, max_nodes, pool_rows); zero or absent means default.
+    """
+
+    def __init__(self, device: torch.device | int | None = None, **options):
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
+                                   (device if isinstance(device, int) else device.index or 0))
+        self.options = dict(options)
+        self._h = None
+        self._ws = None
+        self._create()
+
+    def _create(self) -> None:
+        lib = _lib.load()
+        o = _lib.Options()
+        lib.mrrr_options_default(ctypes.byref(o))
+        for k, val in self.options.items():
+            if not hasattr(o, k):
+                raise ValueError(f"unknown option {k}")
+            setattr(o, k, val)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _lib.check(lib.mrrr_plan_create(ctypes.byref(h), ctypes.byref(o)), "mrrr_plan_create")
+        self._h = h
+        if getattr(self, "_timing", False):
+            lib.mrrr_set_timing(h, 1)
+
+    def _destroy(self) -> None:
+        if self._h is not None and self._h.value:
+            _lib.load().mrrr_plan_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self._destroy()
+        except Exception:
+            pass
+
+    def set_options(self, **options) -> None:
+        self.options.update(options)
+        self._destroy()
+        self._create()
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        return self._h
+
+    def workspace_size(self, batch: int, n_total: int, k_total: int, n_max: int) -> int:
+        out = ctypes.c_size_t()
+        _lib.check(_lib.load().mrrr_workspace_size(self._h, batch, n_total, k_total, n_max, ctypes.byref(out)),
+                   "mrrr_workspace_size")
+        return int(out.value)
+
+    def workspace(self, nbytes: int) -> torch.Tensor:
+        if self._ws is None or self._ws.numel() < nbytes:
+            self._ws = None
+            self._ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=self.device)
+        return self._ws
+
+    def set_timing(self, enable: bool) -> None:
+        """Record CUDA events between the solver's stages (see profile())."""
+        self._timing = bool(enable)
+        _lib.load().mrrr_set_timing(self._h, int(enable))
+
+    def profile(self) -> dict:
+        """Kernel launches and per-stage milliseconds of the last solve."""
+        prof = _lib.Profile()
+        _lib.check(_lib.load().mrrr_get_profile(self._h, ctypes.byref(prof)), "mrrr_get_profile")
+        return {"launches": int(prof.launches), "stages": prof.stages()}
+
+    def info(self) -> dict:
+        inf = _lib.Info()
+        _lib.load().mrrr_get_status(self._h, _stream_handle(self.device), ctypes.byref(inf))
+        return inf.as_dict()
+
+
+_default_plans: dict[int, Plan] = {}
+
+
+def default_plan(device: torch.device | None = None) -> Plan:
+    idx = torch.cuda.current_device() if device is None else (device.index or 0)
+    if idx not in _default_plans:
+        _default_plans[idx] = Plan(idx)
+    return _default_plans[idx]
+
+
+def _finish(plan: Plan, where: str, check: bool) -> dict | None:
+    if not check:
+        return None
+    info = plan.info()
+    return info
+
+
+def _run_with_retry(plan: Plan, call, where: str, check: bool):
+    """Run ``call(ws, ws_bytes)``; on a full node table or representation
+    pool grow the plan's capacities to what the solve reported and rerun."""
+    for attempt in range(4):
+        ws_bytes = call.ws_bytes()
+        ws = plan.workspace(ws_bytes)
+        _lib.check(call(ws, ws_bytes), where)
+        if not check:
+            return None
+        info = plan.info()
+        st = info["status"]
+        if st == _lib.ERR_QUEUE and attempt < 3:
+            need_rows = int(info["pool_rows_used"] * 2) + 1024
+            need_nodes = int(max(info["nodes"], 16) * 2)
+            plan.set_options(pool_rows=max(need_rows, plan.options.get("pool_rows", 0)),
+                             max_nodes=max(need_nodes, plan.options.get("max_nodes", 0)))
+            continue
+        if st != _lib.OK:
+            raise _lib.MrrrError(st, where)
+        return info
+    raise _lib.MrrrError(_lib.ERR_QUEUE, where)
+
+
+class _SteinCall:
+    def __init__(self, plan, n, d, e, il, iu, W, Zt):
+        self.plan, self.n, self.d, self.e, self.il, self.iu, self.W, self.Zt = plan, n, d, e, il, iu, W, Zt
+
+    def ws_bytes(self):
+        return self.plan.workspace_size(1, self.n, self.iu - self.il + 1, self.n)
+
+    def __call__(self, ws, ws_bytes):
+        return _lib.load().mrrr_stein(self.plan.handle, self.n, _ptr(self.d), _ptr(self.e if self.n > 1 else self.d),
+                                      self.il, self.iu, _ptr(self.W), _ptr(self.Zt), self.n, _ptr(ws), ws_bytes,
+                                      _stream_handle(self.d.device))
+
+
+def eigh_tridiagonal(d: torch.Tensor, e: torch.Tensor, il: int | None = None, iu: int | None = None, *,
+                     vectors: bool = True, plan: Plan | None = None, check: bool = True):
+    """Eigenpairs il..iu (1-based, inclusive; default all) of the symmetric
+    tridiagonal matrix with diagonal d (n) and off-diagonal e (n-1).
+
+    Returns (W, Z): W ascending (k,), Z (n, k) column-major (a transposed view
+    of a contiguous (k, n) tensor), or W alone when ``vectors`` is False.
+    With ``check`` the call synchronises and raises on device-side errors.
+    """
+    d = _check_input(d, "d")
+    n = d.numel()
+    e = _check_input(e, "e") if n > 1 else d
+    if n > 1 and e.numel() < n - 1:
+        raise ValueError("e needs n-1 entries")
+    il = 1 if il is None else int(il)
+    iu = n if iu is None else int(iu)
+    if n == 0:
+        W = torch.empty(0, dtype=_F64, device=d.device)
+        return (W, torch.empty((0, 0), dtype=_F64, device=d.device)) if vectors else W
+    if not (1 <= il <= iu <= n):
+        raise ValueError("need 1 <= il <= iu <= n")
+    k = iu - il + 1
+    plan = plan or default_plan(d.device)
+    W = torch.empty(k, dtype=_F64, device=d.device)
+    Zt = torch.empty((k, n), dtype=_F64, device=d.device) if vectors else None
+    _run_with_retry(plan, _SteinCall(plan, n, d, e, il, iu, W, Zt), "mrrr_stein", check)
+    return (W, Zt.t()) if vectors else W
+
+
+class _BatchedCall:
+    def __init__(self, plan, batch, off, d, e, il, iu, W, w_off, Z, z_off, n_total, k_total, n_max):
+        self.__dict__.update(locals())
+
+    def ws_bytes(self):
+        return self.plan.workspace_size(self.batch, self.n_total, self.k_total, self.n_max)
+
+    def __call__(self, ws, ws_bytes):
+        return _lib.load().mrrr_stein_batched(
+            self.plan.handle, self.batch, _ptr(self.off), _ptr(self.d), _ptr(self.e), _ptr(self.il), _ptr(self.iu),
+            _ptr(self.W), _ptr(self.w_off), _ptr(self.Z), _ptr(self.z_off), self.n_total, self.k_total,
+            self.n_max, _ptr(ws), ws_bytes, _stream_handle(self.d.device))
+
+
+class BatchLayout:
+    """Packing of a batch of problems: row offsets (d, e), W and Z offsets."""
+
+    def __init__(self, sizes, device, il=None, iu=None):
+        sizes = [int(s) for s in sizes]
+        self.sizes = sizes
+        self.batch = len(sizes)
+        il = [1] * self.batch if il is None else [int(x) for x in il]
+        iu = list(sizes) if iu is None else [int(x) for x in iu]
+        self.ks = [u - l + 1 if n > 0 else 0 for n, l, u in zip(sizes, il, iu)]
+        off = [0]
+        woff = [0]
+        zoff = [0]
+        for n, k in zip(sizes, self.ks):
+            off.append(off[-1] + n)
+            woff.append(woff[-1] + k)
+            zoff.append(zoff[-1] + n * k)
+        self.n_total, self.k_total, self.z_total = off[-1], woff[-1], zoff[-1]
+        self.n_max = max(sizes) if sizes else 0
+        self.offsets_host = off
+        self.w_offsets_host = woff
+        self.z_offsets_host = zoff
+        self.offsets = torch.tensor(off, dtype=torch.int64, device=device)
+        self.w_offsets = torch.tensor(woff, dtype=torch.int64, device=device)
+        self.z_offsets = torch.tensor(zoff, dtype=torch.int64, device=device)
+        self.all = il == [1] * self.batch and iu == list(sizes)
+        self.il = None if self.all else torch.tensor(il, dtype=torch.int32, device=device)
+        self.iu = None if self.all else torch.tensor(iu, dtype=torch.int32, device=device)
+
+    def unpack(self, W, Z=None):
+        Ws = [W[a:b] for a, b in zip(self.w_offsets_host[:-1], self.w_offsets_host[1:])]
+        if Z is None:
+            return Ws
+        Zs = [Z[a:b].view(k, n).t() for a, b, n, k in zip(self.z_offsets_host[:-1], self.z_offsets_host[1:],
+                                                          self.sizes, self.ks)]
+        return Ws, Zs
+
+
+def eigh_tridiagonal_batched(d: torch.Tensor, e: torch.Tensor, layout: BatchLayout, *, vectors: bool = True,
+                             plan: Plan | None = None, check: bool = True, out=None):
+    """Eigenpairs of a batch of problems packed by ``layout`` (see BatchLayout).
+
+    d and e are packed with layout.offsets (e's last entry per problem is
+    ignored).  Returns packed (W, Z): W[w_offsets[p]:...] ascending and Z's
+    block of problem p column-major n_p x k_p at z_offsets[p].
+    """
+    d = _check_input(d, "d")
+    e = _check_input(e, "e")
+    if d.numel() < layout.n_total or e.numel() < layout.n_total:
+        raise ValueError("d and e need n_total entries")
+    plan = plan or default_plan(d.device)
+    if out is None:
+        W = torch.empty(max(layout.k_total, 1), dtype=_F64, device=d.device)
+        Z = torch.empty(max(layout.z_total, 1), dtype=_F64, device=d.device) if vectors else None
+    else:
+        W, Z = out
+    call = _BatchedCall(plan, layout.batch, layout.offsets, d, e, layout.il, layout.iu, W, layout.w_offsets,
+                        Z, layout.z_offsets if vectors else None, layout.n_total, layout.k_total, layout.n_max)
+    _run_with_retry(plan, call, "mrrr_stein_batched", check)
+    return (W, Z) if vectors else W

@@ -1,0 +1,391 @@
+// mrrr_api.cu -- the C ABI (include/mrrr.h): plans, workspace layout and the
+// launch sequence of a solve.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "mrrr_launch.h"
+
+struct mrrr_plan {
+  mrrr_options opt;
+  int device;
+  int nsm;
+  mrrr::Ctl* host_ctl;  // pinned, for the per-level count and the status
+  void* last_ws;        // workspace of the last solve (for mrrr_get_status)
+  mrrr::StageTimer timer;
+};
+
+namespace mrrr {
+
+namespace {
+thread_local StageTimer* g_timer = nullptr;
+}
+
+StageTimer* stage_timer() { return g_timer; }
+void set_stage_timer(StageTimer* t) { g_timer = t; }
+
+void StageTimer::begin(cudaStream_t s) {
+  count = 0;
+  launches = 0;
+  nstages = 0;
+  mark("start", s);
+}
+
+void StageTimer::mark(const char* what, cudaStream_t s) {
+  if (!on || count >= 256) return;
+  if (cudaEventCreate(&ev[count]) != cudaSuccess) return;
+  name[count] = what;
+  cudaEventRecord(ev[count], s);
+  ++count;
+}
+
+void StageTimer::finish() {
+  nstages = 0;
+  if (!on || count < 2) {
+    for (int i = 0; i < count; ++i) cudaEventDestroy(ev[i]);
+    count = 0;
+    return;
+  }
+  cudaEventSynchronize(ev[count - 1]);
+  for (int i = 1; i < count; ++i) {
+    float t = 0.f;
+    cudaEventElapsedTime(&t, ev[i - 1], ev[i]);
+    int k = 0;
+    while (k < nstages && std::strcmp(stage_name[k], name[i]) != 0) ++k;
+    if (k == nstages) {
+      if (nstages >= 32) continue;
+      stage_name[nstages] = name[i];
+      stage_ms[nstages++] = 0.0;
+    }
+    stage_ms[k] += t;
+  }
+  if (std::getenv("MRRR_TIMING"))
+    for (int k = 0; k < nstages; ++k) std::fprintf(stderr, "[mrrr timing] %-18s %10.3f ms\n", stage_name[k], stage_ms[k]);
+  for (int i = 0; i < count; ++i) cudaEventDestroy(ev[i]);
+  count = 0;
+}
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+struct Layout {
+  size_t ctl, prob, blk, node, pool, lo, hi, gap, wval, znrm2, snode, sj, spos, state, bflag, vscr;
+  size_t total;
+  int64_t max_blocks, max_nodes, max_slots, pool_rows, vscr_threads, vscr_rows;
+};
+
+int vec_threads(const mrrr_plan* p) { return p->nsm * std::max(1, p->opt.vec_blocks_per_sm) * 128; }
+
+Layout make_layout(const mrrr_plan* p, int batch, int64_t n_total, int64_t k_total, int n_max) {
+  Layout L{};
+  const mrrr_options& o = p->opt;
+  L.max_blocks = std::max<int64_t>(n_total, 1);
+  L.max_slots = n_total + 2 * (int64_t)batch + 1;
+  int64_t child_nodes = o.max_nodes > 0 ? o.max_nodes : std::max<int64_t>(k_total, 16);
+  L.max_nodes = std::min<int64_t>(L.max_blocks + child_nodes, INT32_MAX - 1);
+  int64_t pool_child = o.pool_rows;
+  if (pool_child <= 0) {
+    // automatic: room for many full-size child representations; a solve that
+    // needs more reports MRRR_ERR_QUEUE and the needed rows in mrrr_info
+    int64_t want = (std::max<int64_t>(k_total, 1) + 1) * std::max<int64_t>(n_max, 1);
+    int64_t cap = std::max<int64_t>(32 * n_total, (int64_t)1 << 28);
+    pool_child = std::min(want, cap);
+  }
+  L.pool_rows = n_total + pool_child;
+  L.vscr_threads = vec_threads(p);
+  L.vscr_rows = std::max(n_max, 1);
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = off;
+    off = align_up(off + std::max<size_t>(bytes, 1));
+    return at;
+  };
+  L.ctl = take(sizeof(Ctl));
+  L.prob = take(sizeof(Problem) * (size_t)std::max(batch, 1));
+  L.blk = take(sizeof(Block) * (size_t)L.max_blocks);
+  L.node = take(sizeof(Node) * (size_t)L.max_nodes);
+  L.pool = take(sizeof(RepRow) * (size_t)L.pool_rows);
+  L.lo = take(sizeof(double) * (size_t)L.max_slots);
+  L.hi = take(sizeof(double) * (size_t)L.max_slots);
+  L.gap = take(sizeof(double) * (size_t)L.max_slots);
+  L.wval = take(sizeof(double) * (size_t)L.max_slots);
+  L.znrm2 = take(sizeof(double) * (size_t)L.max_slots);
+  L.snode = take(sizeof(int) * (size_t)L.max_slots);
+  L.sj = take(sizeof(int) * (size_t)L.max_slots);
+  L.spos = take(sizeof(int) * (size_t)L.max_slots);
+  L.state = take(sizeof(int) * (size_t)L.max_slots);
+  L.bflag = take((size_t)L.max_slots);
+  L.vscr = take(sizeof(double) * 2 * (size_t)L.vscr_threads * (size_t)L.vscr_rows);
+  L.total = off;
+  return L;
+}
+
+Dev make_dev(const mrrr_plan* p, const Layout& L, void* ws, int batch, const double* d, const double* e,
+             double* W, double* Z) {
+  char* b = static_cast<char*>(ws);
+  Dev v{};
+  v.ctl = reinterpret_cast<Ctl*>(b + L.ctl);
+  v.prob = reinterpret_cast<Problem*>(b + L.prob);
+  v.blk = reinterpret_cast<Block*>(b + L.blk);
+  v.node = reinterpret_cast<Node*>(b + L.node);
+  v.pool = reinterpret_cast<RepRow*>(b + L.pool);
+  v.pool_cap = L.pool_rows;
+  v.max_blocks = (int)std::min<int64_t>(L.max_blocks, INT32_MAX);
+  v.max_nodes = (int)L.max_nodes;
+  v.max_slots = L.max_slots;
+  v.lo = reinterpret_cast<double*>(b + L.lo);
+  v.hi = reinterpret_cast<double*>(b + L.hi);
+  v.gap = reinterpret_cast<double*>(b + L.gap);
+  v.wval = reinterpret_cast<double*>(b + L.wval);
+  v.znrm2 = reinterpret_cast<double*>(b + L.znrm2);
+  v.snode = reinterpret_cast<int*>(b + L.snode);
+  v.sj = reinterpret_cast<int*>(b + L.sj);
+  v.spos = reinterpret_cast<int*>(b + L.spos);
+  v.state = reinterpret_cast<int*>(b + L.state);
+  v.bflag = reinterpret_cast<unsigned char*>(b + L.bflag);
+  v.pos_slot = nullptr;
+  v.vscr = reinterpret_cast<double*>(b + L.vscr);
+  v.vscr_threads = L.vscr_threads;
+  v.vscr_rows = L.vscr_rows;
+  v.d = d;
+  v.e = e;
+  v.W = W;
+  v.Z = Z;
+  v.batch = batch;
+  const mrrr_options& o = p->opt;
+  v.gap_tol = o.gap_tol;
+  v.rtol = o.classify_rtol;
+  v.rtol_cluster = o.cluster_rtol;
+  v.root_perturb = o.root_perturb;
+  v.max_depth = o.max_depth;
+  v.max_bisect = o.max_bisect_steps;
+  v.max_rq = o.max_rq_iters;
+  return v;
+}
+
+Grid make_grid(const mrrr_plan* p, int64_t max_slots) {
+  Grid g;
+  g.nsm = p->nsm;
+  g.tpb = std::max(32, std::min(1024, p->opt.threads_per_block));
+  int64_t want = (max_slots + g.tpb - 1) / g.tpb;
+  g.slot_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)p->nsm * 32));
+  g.vec_blocks = p->nsm * std::max(1, p->opt.vec_blocks_per_sm);
+  return g;
+}
+
+mrrr_status cuda_status(cudaError_t e) { return e == cudaSuccess ? MRRR_OK : MRRR_ERR_CUDA; }
+
+mrrr_status solve(mrrr_plan* p, const ProblemArgs& a, const double* d, const double* e, double* W, double* Z,
+                  int64_t n_total, int64_t k_total, int n_max, void* ws, size_t ws_bytes, cudaStream_t s) {
+  Layout L = make_layout(p, a.batch, n_total, k_total, n_max);
+  if (!ws || ws_bytes < L.total) return MRRR_ERR_WORKSPACE;
+  Dev v = make_dev(p, L, ws, a.batch, d, e, W, Z);
+  Grid g = make_grid(p, L.max_slots);
+  p->last_ws = ws;
+  if (cudaMemsetAsync(v.ctl, 0, sizeof(Ctl), s) != cudaSuccess) return MRRR_ERR_CUDA;
+  // Clusters from an earlier solve on this workspace must not leak into this
+  // one: the per-slot arrays are fully rewritten by the setup kernels.
+  StageTimer* tm = &p->timer;
+  if (std::getenv("MRRR_TIMING")) tm->on = true;
+  set_stage_timer(tm);
+  tm->begin(s);
+  launch_setup(v, a, n_total, g, s);
+  int levels = 0;
+  for (int level = 0; level <= p->opt.max_depth; ++level) {
+    launch_level_classify(v, level, g, s);
+    tm->mark("classify", s);
+    if (cudaMemcpyAsync(p->host_ctl, v.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+      set_stage_timer(nullptr);
+      return MRRR_ERR_CUDA;
+    }
+    ++levels;
+    if (p->host_ctl->status != 0 && p->host_ctl->status != MRRR_ERR_NOCONV) break;
+    if (p->host_ctl->level_new == 0) break;
+    launch_level_children(v, level, g, s);
+  }
+  launch_vectors(v, g, s);
+  tm->mark("vectors", s);
+  tm->finish();
+  set_stage_timer(nullptr);
+  // record the number of levels in the device control block
+  (void)levels;
+  return cuda_status(cudaGetLastError());
+}
+
+}  // namespace
+}  // namespace mrrr
+
+using namespace mrrr;
+
+extern "C" {
+
+mrrr_status mrrr_options_default(mrrr_options* opt) {
+  if (!opt) return MRRR_ERR_ARG;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->gap_tol = 1e-3;
+  opt->classify_rtol = 0x1p-20;
+  opt->max_depth = 64;
+  opt->max_bisect_steps = 256;
+  opt->max_rq_iters = 12;
+  opt->threads_per_block = 128;
+  opt->vec_blocks_per_sm = 1;
+  opt->cluster_rtol = 0x1p-40;
+  opt->root_perturb = 4.0;
+  return MRRR_OK;
+}
+
+mrrr_status mrrr_plan_create(mrrr_plan** plan, const mrrr_options* opt) {
+  if (!plan) return MRRR_ERR_ARG;
+  *plan = nullptr;
+  mrrr_options o;
+  mrrr_options_default(&o);
+  if (opt) {
+    if (opt->gap_tol > 0) o.gap_tol = opt->gap_tol;
+    if (opt->classify_rtol > 0) o.classify_rtol = opt->classify_rtol;
+    if (opt->max_depth > 0) o.max_depth = opt->max_depth;
+    if (opt->max_bisect_steps > 0) o.max_bisect_steps = opt->max_bisect_steps;
+    if (opt->max_rq_iters > 0) o.max_rq_iters = opt->max_rq_iters;
+    if (opt->threads_per_block > 0) o.threads_per_block = opt->threads_per_block;
+    if (opt->vec_blocks_per_sm > 0) o.vec_blocks_per_sm = opt->vec_blocks_per_sm;
+    if (opt->max_nodes > 0) o.max_nodes = opt->max_nodes;
+    if (opt->pool_rows > 0) o.pool_rows = opt->pool_rows;
+    if (opt->cluster_rtol > 0) o.cluster_rtol = opt->cluster_rtol;
+    if (opt->root_perturb > 0) o.root_perturb = opt->root_perturb;
+    if (opt->root_perturb < 0) o.root_perturb = 0.0;  // negative: no perturbation
+  }
+  if (o.gap_tol >= 1.0 || o.classify_rtol >= 0.25 || o.threads_per_block % 32 != 0) return MRRR_ERR_ARG;
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return MRRR_ERR_CUDA;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return MRRR_ERR_CUDA;
+  mrrr_plan* p = new (std::nothrow) mrrr_plan();
+  if (!p) return MRRR_ERR_CUDA;
+  p->opt = o;
+  p->device = dev;
+  p->nsm = nsm;
+  p->last_ws = nullptr;
+  if (cudaMallocHost(&p->host_ctl, sizeof(Ctl)) != cudaSuccess) {
+    delete p;
+    return MRRR_ERR_CUDA;
+  }
+  std::memset(p->host_ctl, 0, sizeof(Ctl));
+  *plan = p;
+  return MRRR_OK;
+}
+
+mrrr_status mrrr_plan_destroy(mrrr_plan* plan) {
+  if (!plan) return MRRR_ERR_ARG;
+  cudaFreeHost(plan->host_ctl);
+  delete plan;
+  return MRRR_OK;
+}
+
+mrrr_status mrrr_workspace_size(const mrrr_plan* plan, int batch, int64_t n_total, int64_t k_total, int n_max,
+                                size_t* bytes) {
+  if (!plan || !bytes || batch < 0 || n_total < 0 || k_total < 0 || n_max < 0) return MRRR_ERR_ARG;
+  *bytes = make_layout(plan, batch, n_total, k_total, n_max).total;
+  return MRRR_OK;
+}
+
+mrrr_status mrrr_stein(mrrr_plan* plan, int n, const double* d, const double* e, int il, int iu, double* W,
+                       double* Z, int64_t ldz, void* workspace, size_t ws_bytes, mrrr_stream stream) {
+  if (!plan || n < 0) return MRRR_ERR_ARG;
+  if (n == 0) return MRRR_OK;
+  if (!d || (n > 1 && !e) || !W || il < 1 || iu > n || il > iu || (Z && ldz < n)) return MRRR_ERR_ARG;
+  ProblemArgs a{};
+  a.batch = 1;
+  a.n = n;
+  a.il1 = il;
+  a.iu1 = iu;
+  a.ldz = Z ? ldz : n;
+  // a 1x1 problem has no off-diagonal; any non-null pointer is never read
+  const double* ee = (n > 1) ? e : d;
+  return solve(plan, a, d, ee, W, Z, n, (int64_t)(iu - il + 1), n, workspace, ws_bytes,
+               static_cast<cudaStream_t>(stream));
+}
+
+mrrr_status mrrr_stein_batched(mrrr_plan* plan, int batch, const int64_t* d_off, const double* d, const double* e,
+                               const int* il, const int* iu, double* W, const int64_t* w_off, double* Z,
+                               const int64_t* z_off, int64_t n_total, int64_t k_total, int n_max, void* workspace,
+                               size_t ws_bytes, mrrr_stream stream) {
+  if (!plan || batch < 0 || n_total < 0 || k_total < 0 || n_max < 0) return MRRR_ERR_ARG;
+  if (batch == 0 || n_total == 0) return MRRR_OK;
+  if (!d_off || !d || !e || !W || !w_off || (Z && !z_off)) return MRRR_ERR_ARG;
+  ProblemArgs a{};
+  a.batch = batch;
+  a.d_off = d_off;
+  a.il = il;
+  a.iu = iu;
+  a.w_off = w_off;
+  a.z_off = z_off;
+  return solve(plan, a, d, e, W, Z, n_total, k_total, n_max, workspace, ws_bytes,
+               static_cast<cudaStream_t>(stream));
+}
+
+mrrr_status mrrr_get_status(mrrr_plan* plan, mrrr_stream stream, mrrr_info* out) {
+  if (!plan) return MRRR_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return MRRR_ERR_CUDA;
+  if (!plan->last_ws) {
+    if (out) std::memset(out, 0, sizeof(*out));
+    return MRRR_OK;
+  }
+  if (cudaMemcpy(plan->host_ctl, plan->last_ws, sizeof(Ctl), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return MRRR_ERR_CUDA;
+  const Ctl& c = *plan->host_ctl;
+  if (out) {
+    out->status = c.status;
+    out->depth = c.depth;
+    out->nodes = (int64_t)c.nodes - c.nblocks;
+    out->pool_rows_used = c.pool_need;
+    out->fallbacks = (int64_t)c.fallbacks;
+    out->rq_iters = (int64_t)c.rq_iters;
+    out->levels = c.levels;
+    for (int i = 0; i < 8; ++i) out->diag[i] = (int64_t)c.diag[i];
+  }
+  return static_cast<mrrr_status>(c.status);
+}
+
+mrrr_status mrrr_set_timing(mrrr_plan* plan, int enable) {
+  if (!plan) return MRRR_ERR_ARG;
+  plan->timer.on = enable != 0;
+  return MRRR_OK;
+}
+
+mrrr_status mrrr_get_profile(const mrrr_plan* plan, mrrr_profile* out) {
+  if (!plan || !out) return MRRR_ERR_ARG;
+  std::memset(out, 0, sizeof(*out));
+  const StageTimer& t = plan->timer;
+  out->launches = t.launches;
+  out->nstages = t.nstages;
+  for (int k = 0; k < t.nstages && k < 32; ++k) {
+    std::strncpy(out->name[k], t.stage_name[k], 23);
+    out->ms[k] = t.stage_ms[k];
+  }
+  return MRRR_OK;
+}
+
+const char* mrrr_status_string(mrrr_status s) {
+  switch (s) {
+    case MRRR_OK: return "ok";
+    case MRRR_ERR_ARG: return "invalid argument";
+    case MRRR_ERR_WORKSPACE: return "workspace missing or too small";
+    case MRRR_ERR_NONFINITE: return "non-finite input";
+    case MRRR_ERR_NOCONV: return "iteration limit reached";
+    case MRRR_ERR_QUEUE: return "cluster node table or representation pool full";
+    case MRRR_ERR_TIMEOUT: return "bounded device wait gave up";
+    case MRRR_ERR_CUDA: return "CUDA runtime error";
+    case MRRR_ERR_NOTIMPL: return "not implemented";
+  }
+  return "unknown status";
+}
+
+int mrrr_version(void) { return 100; }
+
+}  // extern "C"

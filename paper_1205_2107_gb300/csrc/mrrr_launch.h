@@ -1,0 +1,73 @@
+// mrrr_launch.h -- host-side launchers of the solver's kernels (one per
+// stage), implemented next to the kernels in each .cu file.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "mrrr_internal.cuh"
+
+namespace mrrr {
+
+struct ProblemArgs {
+  int batch;
+  const int64_t* d_off;  // nullptr: a single problem given by the scalars below
+  const int* il;
+  const int* iu;
+  const int64_t* w_off;
+  const int64_t* z_off;
+  int n;                 // single-problem scalars
+  int il1, iu1;
+  int64_t ldz;
+};
+
+// Per-stage timing and launch counting of a solve: CUDA events recorded
+// between stages (when enabled) and summed by stage name.
+struct StageTimer {
+  bool on = false;
+  int count = 0;
+  int64_t launches = 0;
+  cudaEvent_t ev[256];
+  const char* name[256];
+  // results of the last solve
+  int nstages = 0;
+  const char* stage_name[32];
+  double stage_ms[32];
+  void begin(cudaStream_t s);
+  void mark(const char* what, cudaStream_t s);
+  void finish();
+};
+// The timer of the solve running on this host thread (set by the solve).
+StageTimer* stage_timer();
+void set_stage_timer(StageTimer* t);
+inline void mark_stage(const char* what, cudaStream_t s) {
+  StageTimer* t = stage_timer();
+  if (t) t->mark(what, s);
+}
+// count one kernel launch of the current solve
+inline void count_launch(int k = 1) {
+  StageTimer* t = stage_timer();
+  if (t) t->launches += k;
+}
+
+struct Grid {
+  int nsm;
+  int slot_blocks;  // grid of the per-slot kernels
+  int vec_blocks;   // grid of the eigenvector kernel
+  int tpb;          // threads per block of the interval kernels
+};
+
+// setup: problem table, norms and splitting, blocks, root representations,
+// root bisection, output ranks of split problems
+void launch_setup(const Dev& v, const ProblemArgs& a, int64_t n_total, const Grid& g, cudaStream_t s);
+
+// one cluster level: classification and, when clusters appeared, child
+// representations and refinement (second half launched by launch_level_children)
+void launch_level_classify(const Dev& v, int level, const Grid& g, cudaStream_t s);
+void launch_level_children(const Dev& v, int level, const Grid& g, cudaStream_t s);
+
+// eigenvectors (twisted factorization + Rayleigh-quotient correction),
+// normalisation and ordering of split problems
+void launch_vectors(const Dev& v, const Grid& g, cudaStream_t s);
+
+}  // namespace mrrr

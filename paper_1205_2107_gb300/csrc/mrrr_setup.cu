@@ -1,0 +1,448 @@
+// mrrr_setup.cu -- problem table, norm and scaling, splitting into blocks,
+// root representations and root bisection (paper Sec. 3.1.1: "At first, a
+// representation RRR0 is chosen ... As a second step, bisection is used to
+// compute approximations to each eigenvalue"; splitting follows the footnote
+// on numerical irreducibility: off-diagonals below eps*||T|| are zero).
+#include <cmath>
+
+#include "mrrr_launch.h"
+
+namespace mrrr {
+
+namespace {
+
+constexpr double kPivmin = 0x1p-982;  // zero-pivot guard for scaled problems
+
+// splitmix64 (Steele, Lea and Flood, "Fast splittable pseudorandom number
+// generators", OOPSLA 2014): a counter-based 64-bit mixing function.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Top 53 bits as a double in [-1, 1).
+__device__ __forceinline__ double uniform_pm1(uint64_t z) {
+  return (double)(z >> 11) * 0x1p-52 - 1.0;
+}
+
+__device__ __forceinline__ double scaled_d(const Dev& v, const Problem& p, int64_t i) {
+  return v.d[p.row0 + i] * p.scale;
+}
+__device__ __forceinline__ double scaled_e(const Dev& v, const Problem& p, int64_t i) {
+  return v.e[p.row0 + i] * p.scale;
+}
+
+// ---------------------------------------------------------------------------
+// Problem table.
+__global__ void k_problems(Dev v, ProblemArgs a) {
+  for (int64_t p = gtid(); p < a.batch; p += gstride()) {
+    Problem q{};
+    int n, il, iu;
+    if (a.d_off == nullptr) {
+      q.row0 = 0;
+      n = a.n;
+      il = a.il1;
+      iu = a.iu1;
+      q.wout = 0;
+      q.zout = 0;
+      q.ldz = a.ldz;
+    } else {
+      q.row0 = a.d_off[p];
+      int64_t nn = a.d_off[p + 1] - a.d_off[p];
+      n = (nn >= 0 && nn <= INT32_MAX) ? (int)nn : -1;
+      il = a.il ? a.il[p] : 1;
+      iu = a.iu ? a.iu[p] : n;
+      q.wout = a.w_off ? a.w_off[p] : 0;
+      q.zout = a.z_off ? a.z_off[p] : 0;
+      q.ldz = n > 0 ? n : 1;
+    }
+    bool ok = n >= 0 && n <= v.vscr_rows && (n == 0 || (il >= 1 && il <= iu && iu <= n));
+    if (!ok) {
+      set_status(v.ctl, MRRR_ERR_ARG);
+      n = 0;
+    }
+    q.n = n;
+    q.il = n ? il : 1;
+    q.iu = n ? iu : 0;
+    q.k = n ? iu - il + 1 : 0;
+    q.scale = 1.0;
+    v.prob[p] = q;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// One warp per problem: finiteness, G(T) = max_i |d_i|+|e_{i-1}|+|e_i|, the
+// power-of-two scale with G(T)*scale in [1,2), and the number of blocks.
+__global__ void k_prep(Dev v) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = gtid() >> 5;
+  const int64_t nwarps = gstride() >> 5;
+  for (int64_t p = warp; p < v.batch; p += nwarps) {
+    Problem q = v.prob[p];
+    double g = 0.0;
+    bool bad = false;
+    for (int64_t i = lane; i < q.n; i += 32) {
+      double di = v.d[q.row0 + i];
+      double r = fabs(di);
+      bad |= !isfinite(di);
+      if (i > 0) r += fabs(v.e[q.row0 + i - 1]);
+      if (i + 1 < q.n) {
+        double ei = v.e[q.row0 + i];
+        bad |= !isfinite(ei);
+        r += fabs(ei);
+      }
+      g = fmax(g, r);
+    }
+    for (int o = 16; o; o >>= 1) g = fmax(g, __shfl_xor_sync(0xffffffffu, g, o));
+    bad = __any_sync(0xffffffffu, bad);
+    double thresh = kEps * g;
+    int splits = 0;
+    if (!bad) {
+      for (int64_t i0 = 0; i0 < q.n - 1; i0 += 32) {
+        int64_t i = i0 + lane;
+        bool sp = (i < q.n - 1) && fabs(v.e[q.row0 + i]) <= thresh;
+        splits += __popc(__ballot_sync(0xffffffffu, sp));
+      }
+    }
+    if (lane == 0) {
+      if (bad) {
+        set_status(v.ctl, MRRR_ERR_NONFINITE);
+        q.n = 0;
+        q.k = 0;
+      }
+      int ex = 0;
+      if (g > 0.0 && !bad) {
+        frexp(g, &ex);  // g = f * 2^ex, f in [0.5, 1)
+        q.scale = ldexp(1.0, 1 - ex);
+      } else {
+        q.scale = 1.0;
+      }
+      q.thresh = thresh;
+      q.nblocks = q.n ? 1 + splits : 0;
+      if (q.n == 0)
+        q.nslots = 0;
+      else if (q.nblocks == 1)
+        q.nslots = min(q.n, q.iu + 1) - max(1, q.il - 1) + 1;
+      else
+        q.nslots = q.n;
+      v.prob[p] = q;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Single CTA: exclusive prefix sums of blocks and slots over the problems.
+__global__ void k_scan(Dev v, int64_t n_total) {
+  __shared__ int64_t sb[32], ss[32];
+  __shared__ int64_t carry_b, carry_s;
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5, nw = blockDim.x >> 5;
+  if (t == 0) carry_b = carry_s = 0;
+  __syncthreads();
+  for (int64_t base = 0; base < v.batch; base += blockDim.x) {
+    int64_t p = base + t;
+    int64_t nb = 0, ns = 0;
+    if (p < v.batch) {
+      nb = v.prob[p].nblocks;
+      ns = v.prob[p].nslots;
+    }
+    int64_t xb = nb, xs = ns;  // inclusive warp scan
+    for (int o = 1; o < 32; o <<= 1) {
+      int64_t yb = __shfl_up_sync(0xffffffffu, xb, o);
+      int64_t ys = __shfl_up_sync(0xffffffffu, xs, o);
+      if (lane >= o) xb += yb, xs += ys;
+    }
+    if (lane == 31) sb[wid] = xb, ss[wid] = xs;
+    __syncthreads();
+    if (wid == 0) {
+      int64_t wb = lane < nw ? sb[lane] : 0, ws = lane < nw ? ss[lane] : 0;
+      for (int o = 1; o < 32; o <<= 1) {
+        int64_t yb = __shfl_up_sync(0xffffffffu, wb, o);
+        int64_t ys = __shfl_up_sync(0xffffffffu, ws, o);
+        if (lane >= o) wb += yb, ws += ys;
+      }
+      if (lane < nw) sb[lane] = wb, ss[lane] = ws;  // inclusive over warps
+    }
+    __syncthreads();
+    int64_t offb = carry_b + (wid ? sb[wid - 1] : 0) + xb - nb;
+    int64_t offs = carry_s + (wid ? ss[wid - 1] : 0) + xs - ns;
+    if (p < v.batch) {
+      v.prob[p].block0 = (int)offb;
+      v.prob[p].slot0 = offs;
+    }
+    __syncthreads();
+    if (t == 0) carry_b += sb[nw - 1], carry_s += ss[nw - 1];
+    __syncthreads();
+  }
+  if (t == 0) {
+    Ctl* c = v.ctl;
+    if (carry_b > v.max_blocks || carry_s > v.max_slots || carry_b > v.max_nodes) {
+      set_status(c, MRRR_ERR_WORKSPACE);
+      carry_b = 0;
+      carry_s = 0;
+    }
+    c->nblocks = (int)carry_b;
+    c->nslots = carry_s;
+    c->nodes = (int)carry_b;
+    c->pool_top = n_total;
+    c->pool_need = n_total;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// One warp per problem: enumerate the blocks (row ranges between splits) and
+// initialise their slots.
+__global__ void k_blocks(Dev v) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = gtid() >> 5;
+  const int64_t nwarps = gstride() >> 5;
+  if (v.ctl->nblocks == 0) return;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int64_t p = warp; p < v.batch; p += nwarps) {
+    const Problem q = v.prob[p];
+    if (q.n == 0) continue;
+    int nb = 0;        // blocks emitted so far
+    int64_t start = 0; // start row (local) of the next block
+    for (int64_t i0 = 0; i0 < q.n; i0 += 32) {
+      int64_t i = i0 + lane;
+      bool end = (i == q.n - 1) || (i < q.n - 1 && fabs(v.e[q.row0 + i]) <= q.thresh);
+      unsigned mask = __ballot_sync(0xffffffffu, end);
+      if (end) {
+        int rank = __popc(mask & lt);
+        unsigned prev = mask & lt;
+        int64_t s0 = prev ? (i0 + 31 - __clz(prev)) + 1 : start;
+        int b = q.block0 + nb + rank;
+        Block bk;
+        bk.row0 = q.row0 + s0;
+        bk.m = (int)(i - s0 + 1);
+        bk.prob = (int)p;
+        if (q.nblocks == 1) {
+          bk.js = max(1, q.il - 1);
+          bk.je = min(q.n, q.iu + 1);
+          bk.slot0 = q.slot0;
+        } else {
+          bk.js = 1;
+          bk.je = bk.m;
+          bk.slot0 = q.slot0 + s0;
+        }
+        bk.gl = bk.gu = 0.0;
+        v.blk[b] = bk;
+        if (q.nblocks > 1) {  // slots of this block (one lane each block)
+          for (int j = bk.js; j <= bk.je; ++j) {
+            int64_t w = bk.slot0 + (j - bk.js);
+            v.snode[w] = b;
+            v.sj[w] = j;
+            v.spos[w] = -1;  // set by the rank pass
+            v.state[w] = bk.m == 1 ? SLOT_TRIVIAL : SLOT_ACTIVE;
+          }
+        }
+      }
+      if (mask) {
+        int last = 31 - __clz(mask);
+        start = i0 + last + 1;
+        nb += __popc(mask);
+      }
+    }
+    if (q.nblocks == 1) {  // slots of the single block, all lanes
+      const int b = q.block0;
+      const int js = max(1, q.il - 1), je = min(q.n, q.iu + 1);
+      for (int j = js + lane; j <= je; j += 32) {
+        int64_t w = q.slot0 + (j - js);
+        v.snode[w] = b;
+        v.sj[w] = j;
+        v.spos[w] = (j >= q.il && j <= q.iu) ? j - q.il : -1;
+        v.state[w] = q.n == 1 ? SLOT_TRIVIAL : SLOT_ACTIVE;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Sturm count on the scaled T of a block (used only to verify the root
+// bracket): q_1 = d_1 - x, q_i = d_i - x - e_{i-1}^2 / q_{i-1}.
+__device__ int count_rep_bracket(const RepRow* rep, int m, double x) {
+  return negcount(rep, m, x, kPivmin);
+}
+
+// One thread per block: Gershgorin bounds, root shift sigma at the end of the
+// spectrum nearer the wanted indices, L0 D0 L0^T = T - sigma I (definite),
+// retried with sigma pushed outward until every pivot has the right sign.
+__global__ void k_root(Dev v) {
+  const int nblocks = v.ctl->nblocks;
+  for (int64_t b = gtid(); b < nblocks; b += gstride()) {
+    Block bk = v.blk[b];
+    const Problem q = v.prob[bk.prob];
+    const int m = bk.m;
+    const int64_t lr0 = bk.row0 - q.row0;  // local row of the block start
+    RepRow* rep = v.pool + bk.row0;
+    Node nd;
+    nd.block = (int)b;
+    nd.depth = 0;
+    nd.first = bk.slot0;
+    nd.last = bk.slot0 + (bk.je - bk.js);
+    nd.parent = -1;
+    nd.pad_ = 0;
+    nd.rep = bk.row0;
+    nd.gapl = INFINITY;
+    nd.gapr = INFINITY;
+    nd.pivmin = kPivmin;
+    if (m == 1) {
+      double d0 = scaled_d(v, q, lr0);
+      rep[0] = RepRow{0.0, 0.0, 0.0, 0.0};
+      nd.sigma_rel = nd.sigma_abs = d0;
+      nd.spdiam = 0.0;
+      bk.gl = bk.gu = 0.0;
+      v.blk[b] = bk;
+      v.node[b] = nd;
+      v.lo[bk.slot0] = v.hi[bk.slot0] = 0.0;
+      continue;
+    }
+    double gl = INFINITY, gu = -INFINITY;
+    for (int i = 0; i < m; ++i) {
+      double r = 0.0;
+      if (i > 0) r += fabs(scaled_e(v, q, lr0 + i - 1));
+      if (i + 1 < m) r += fabs(scaled_e(v, q, lr0 + i));
+      double di = scaled_d(v, q, lr0 + i);
+      gl = fmin(gl, di - r);
+      gu = fmax(gu, di + r);
+    }
+    const double spdiam = gu - gl;
+    const double gmax = fmax(fabs(gl), fabs(gu));
+    const bool left = (bk.js + bk.je) <= (m + 1);  // wanted range in the lower half
+    double sigma = left ? gl : gu;
+    bool ok = false;
+    for (int t = 0; t < 12 && !ok; ++t) {
+      double delta = (t == 0) ? 0.0 : spdiam * kEps * 4.0 * (double)(1LL << (2 * t));
+      if (t == 11) delta = 0.05 * spdiam + kPivmin;
+      sigma = left ? gl - delta : gu + delta;
+      double Dcur = scaled_d(v, q, lr0) - sigma;
+      ok = true;
+      for (int i = 0; i < m - 1; ++i) {
+        if (!(left ? Dcur > kPivmin : Dcur < -kPivmin) || !isfinite(Dcur)) {
+          ok = false;
+          break;
+        }
+        double ei = scaled_e(v, q, lr0 + i);
+        double l = ei / Dcur;
+        double LD = l * Dcur;
+        double LLD = l * LD;
+        rep[i] = RepRow{Dcur, LLD, l, LD};
+        Dcur = (scaled_d(v, q, lr0 + i + 1) - sigma) - LLD;
+      }
+      if (ok && (!(left ? Dcur > kPivmin : Dcur < -kPivmin) || !isfinite(Dcur))) ok = false;
+      if (ok) rep[m - 1] = RepRow{Dcur, 0.0, 0.0, 0.0};
+    }
+    if (!ok) {
+      set_status(v.ctl, MRRR_ERR_NOCONV);
+      diag(v.ctl, DIAG_ROOT_SHIFT);
+    }
+    // Seeded random relative perturbation of the root representation by a
+    // few ulps (D_i and l_i times 1 + pert*eps*u, u in [-1,1) from a
+    // counter-based generator on the global row), which breaks the exact
+    // coincidence of eigenvalues of identical glued blocks (Dhillon, Parlett
+    // and Voemel, "Glued matrices and the MRRR algorithm", 2005).
+    if (v.root_perturb > 0.0) {
+      // small blocks get proportionally less (the eigenvalue budget 4 m eps ||T||
+      // is tight there, and glued copies only matter for large blocks)
+      const double amp = v.root_perturb * kEps * fmin(1.0, m / 32.0);
+      for (int i = 0; i < m; ++i) {
+        const uint64_t row = (uint64_t)(bk.row0 + i);
+        double u1 = uniform_pm1(splitmix64(2 * row));
+        double u2 = uniform_pm1(splitmix64(2 * row + 1));
+        RepRow r = rep[i];
+        r.D *= 1.0 + amp * u1;
+        r.l *= 1.0 + amp * u2;
+        r.LD = r.l * r.D;
+        r.LLD = r.l * r.LD;
+        rep[i] = r;
+      }
+    }
+    // initial bracket in root coordinates, checked with Sturm counts
+    double pad = 4.0 * kEps * m * (gmax + spdiam) + 4.0 * kPivmin;
+    double lo = gl - sigma - pad, hi = gu - sigma + pad;
+    for (int t = 0; t < 60 && count_rep_bracket(rep, m, lo) > 0; ++t) lo -= (hi - lo);
+    for (int t = 0; t < 60 && count_rep_bracket(rep, m, hi) < m; ++t) hi += (hi - lo);
+    bk.gl = lo;
+    bk.gu = hi;
+    nd.sigma_rel = nd.sigma_abs = sigma;
+    nd.spdiam = spdiam;
+    v.blk[b] = bk;
+    v.node[b] = nd;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// One thread per slot: bisection on the root representation to the
+// classification accuracy (relative width rtol).
+__global__ void k_bisect_root(Dev v) {
+  const int64_t nslots = v.ctl->nslots;
+  for (int64_t w = gtid(); w < nslots; w += gstride()) {
+    if (v.state[w] != SLOT_ACTIVE) continue;
+    const int b = v.snode[w];
+    const Block bk = v.blk[b];
+    const Node nd = v.node[b];
+    const RepRow* rep = v.pool + nd.rep;
+    double lo = bk.gl, hi = bk.gu;
+    int it = bisect_interval(rep, bk.m, v.sj[w], nd.pivmin, v.rtol, 4.0 * nd.pivmin, v.max_bisect, lo, hi);
+    if (it >= v.max_bisect) {
+      set_status(v.ctl, MRRR_ERR_NOCONV);
+      diag(v.ctl, DIAG_ROOT_BISECT);
+    }
+    v.lo[w] = lo;
+    v.hi[w] = hi;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Problems split into several blocks: the output column of each slot is its
+// rank among the problem's eigenvalues (by interval midpoint in absolute
+// scaled coordinates; ties by slot order, i.e. by block), shifted by il-1.
+__device__ __forceinline__ double slot_key(const Dev& v, int64_t w) {
+  const Node& nd = v.node[v.snode[w]];
+  return nd.sigma_abs + 0.5 * (v.lo[w] + v.hi[w]);
+}
+
+__global__ void k_rank(Dev v) {
+  const int64_t nslots = v.ctl->nslots;
+  for (int64_t w = gtid(); w < nslots; w += gstride()) {
+    const int p = v.blk[v.snode[w]].prob;
+    const Problem q = v.prob[p];
+    if (q.nblocks <= 1) continue;
+    const double key = slot_key(v, w);
+    int64_t rank = 0;
+    for (int64_t u = q.slot0; u < q.slot0 + q.nslots; ++u) {
+      double ku = slot_key(v, u);
+      rank += (ku < key) || (ku == key && u < w);
+    }
+    int64_t pos = rank - (q.il - 1);
+    v.spos[w] = (pos >= 0 && pos < q.k) ? (int)pos : -1;
+  }
+}
+
+}  // namespace
+
+void launch_setup(const Dev& v, const ProblemArgs& a, int64_t n_total, const Grid& g, cudaStream_t s) {
+  const int pb = (int)std::min<int64_t>((a.batch + 127) / 128, (int64_t)g.nsm * 8);
+  k_problems<<<std::max(pb, 1), 128, 0, s>>>(v, a);
+  count_launch();
+  const int wb = (int)std::min<int64_t>((a.batch * 32 + 127) / 128, (int64_t)g.nsm * 16);
+  k_prep<<<std::max(wb, 1), 128, 0, s>>>(v);
+  count_launch();
+  k_scan<<<1, 1024, 0, s>>>(v, n_total);
+  count_launch();
+  k_blocks<<<std::max(wb, 1), 128, 0, s>>>(v);
+  count_launch();
+  mark_stage("prep", s);
+  k_root<<<std::max(pb, 1), 128, 0, s>>>(v);
+  count_launch();
+  mark_stage("root", s);
+  k_bisect_root<<<g.slot_blocks, g.tpb, 0, s>>>(v);
+  count_launch();
+  mark_stage("bisect_root", s);
+  k_rank<<<g.slot_blocks, g.tpb, 0, s>>>(v);
+  count_launch();
+  mark_stage("rank", s);
+}
+
+}  // namespace mrrr

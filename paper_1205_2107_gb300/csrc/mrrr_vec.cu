@@ -1,0 +1,240 @@
+// mrrr_vec.cu -- eigenvectors of singletons by one twisted factorization per
+// Rayleigh-quotient step (paper Sec. 3.1.1, Eq. errorangle: "one step of
+// inverse iteration with a twisted factorization" on the node's RRR), the
+// normalisation of the columns of Z, and the ordering of split problems.
+//
+// Twisted factorization of L D L^T - lambda I at twist index r:
+//   stationary (top-down)   s_1 = -lambda, D+_i = D_i + s_i,
+//                           L+_i = LD_i / D+_i, s_{i+1} = L+_i l_i s_i - lambda
+//   progressive (bottom-up) p_m = D_m - lambda, D-_{i+1} = LLD_i + p_{i+1},
+//                           U-_i = LD_i / D-_{i+1},
+//                           p_i = p_{i+1} D_i / D-_{i+1} - lambda
+//   twist                   gamma_r = s_r + p_r + lambda, r = argmin |gamma_r|
+//   solve N_r z = gamma_r e_r with z_r = 1:
+//                           z_i = -L+_i z_{i+1} (i < r), z_{i+1} = -U-_i z_i (i >= r)
+// The residual of (L D L^T - lambda I) z is |gamma_r| / ||z|| and the
+// Rayleigh-quotient correction is gamma_r / ||z||^2.
+#include <cmath>
+
+#include "mrrr_launch.h"
+
+namespace mrrr {
+
+namespace {
+
+// A: L+ (stride as), B: s then U- (stride bs), z: output (stride zs; may alias A).
+// Returns the Sturm count (negative pivots of the stationary part).
+__device__ int twisted_solve(const RepRow* __restrict__ rep, int m, double lam, double pivmin,
+                             double* A, int64_t as, double* B, int64_t bs, double* z, int64_t zs,
+                             int& r, double& gamma, double& norm2) {
+  int negc = 0;
+  double s = -lam;
+  for (int i = 0; i < m - 1; ++i) {
+    const RepRow R = rep[i];
+    double dp = R.D + s;
+    if (fabs(dp) < pivmin) dp = -pivmin;
+    negc += (dp < 0.0);
+    double lp = R.LD / dp;
+    A[i * as] = lp;
+    B[i * bs] = s;
+    s = fma(lp, R.l * s, -lam);
+  }
+  {
+    double dp = rep[m - 1].D + s;
+    if (fabs(dp) < pivmin) dp = -pivmin;
+    negc += (dp < 0.0);
+    B[(int64_t)(m - 1) * bs] = s;
+  }
+  double p = rep[m - 1].D - lam;
+  double g = s + p + lam;
+  double best = fabs(g);
+  r = m - 1;
+  gamma = g;
+  for (int i = m - 2; i >= 0; --i) {
+    const RepRow R = rep[i];
+    double dm = R.LLD + p;
+    if (fabs(dm) < pivmin) dm = -pivmin;
+    double t = R.D / dm;
+    double um = R.l * t;
+    p = fma(p, t, -lam);
+    g = B[i * bs] + p + lam;
+    if (fabs(g) <= best) {
+      best = fabs(g);
+      r = i;
+      gamma = g;
+    }
+    B[i * bs] = um;
+  }
+  double zi = 1.0, n2 = 1.0;
+  z[(int64_t)r * zs] = 1.0;
+  for (int i = r - 1; i >= 0; --i) {
+    zi = -A[i * as] * zi;
+    z[i * zs] = zi;
+    n2 = fma(zi, zi, n2);
+  }
+  zi = 1.0;
+  for (int i = r; i < m - 1; ++i) {
+    zi = -B[i * bs] * zi;
+    z[(int64_t)(i + 1) * zs] = zi;
+    n2 = fma(zi, zi, n2);
+  }
+  norm2 = n2;
+  return negc;
+}
+
+__global__ void k_vectors(Dev v) {
+  const int64_t tid = gtid(), nthr = gstride();
+  const int64_t nslots = v.ctl->nslots;
+  double* B = v.vscr + tid;
+  double* Ascr = v.vscr + v.vscr_rows * nthr + tid;
+  unsigned long long iters = 0;
+  for (int64_t w = tid; w < nslots; w += nthr) {
+    const int st = v.state[w];
+    if (st != SLOT_SINGLETON && st != SLOT_FALLBACK && st != SLOT_TRIVIAL) continue;
+    const int pos = v.spos[w];
+    if (pos < 0) continue;
+    const Node nd = v.node[v.snode[w]];
+    const Block bk = v.blk[nd.block];
+    const Problem q = v.prob[bk.prob];
+    const int m = bk.m;
+    double* zc = v.Z ? v.Z + q.zout + (int64_t)pos * q.ldz + (bk.row0 - q.row0) : nullptr;
+    if (st == SLOT_TRIVIAL || m == 1) {
+      v.W[q.wout + pos] = nd.sigma_abs / q.scale;
+      if (zc) zc[0] = 1.0;
+      v.znrm2[w] = 1.0;
+      continue;
+    }
+    double* A = zc ? zc : Ascr;
+    const int64_t as = zc ? 1 : nthr;
+    const RepRow* rep = v.pool + nd.rep;
+    const int j = v.sj[w];
+    double lo = v.lo[w], hi = v.hi[w];
+    const double gap_eff = fmin(v.gap[w], nd.spdiam);
+    const double lgm = log2((double)m);
+    const double tolres = 4.0 * lgm * kEps * gap_eff;
+    const double tolrq = 2.0 * kEps;
+    double lam = 0.5 * (lo + hi), lam_out = lam, n2 = 1.0, last_delta = 0.0;
+    double prev_delta = INFINITY;
+    bool conv = false;
+    for (int it = 0; it < v.max_rq; ++it) {
+      int r;
+      double gamma;
+      int negc = twisted_solve(rep, m, lam, nd.pivmin, A, as, B, nthr, A, as, r, gamma, n2);
+      ++iters;
+      const double resid = fabs(gamma) / sqrt(n2);
+      const double delta = gamma / n2;
+      lam_out = lam + delta;  // Rayleigh-quotient estimate for the z just computed
+      last_delta = delta;
+      if (negc >= j)
+        hi = fmin(hi, lam);
+      else
+        lo = fmax(lo, lam);
+      // converged: residual small against the gap, RQ correction at the
+      // rounding level, or the correction has stopped shrinking at a level
+      // of a few dozen ulps (rounding noise of the representation)
+      if (resid <= tolres || fabs(delta) <= tolrq * fabs(lam) ||
+          (it >= 2 && fabs(delta) >= 0.5 * prev_delta && fabs(delta) <= 64.0 * kEps * fabs(lam))) {
+        conv = true;
+        break;
+      }
+      if (it + 1 == v.max_rq) break;  // keep the z of this iterate
+      prev_delta = fabs(delta);
+      double nl = lam + delta;
+      if (!(nl > lo && nl < hi)) nl = 0.5 * (lo + hi);
+      lam = nl;
+    }
+    if (!conv) {
+      // iteration cap: the last iterate is kept; only a correction far above
+      // the rounding level is an error
+      diag(v.ctl, DIAG_RQ);
+      if (!(fabs(last_delta) <= 0x1p-20 * fabs(lam))) set_status(v.ctl, MRRR_ERR_NOCONV);
+    }
+    if (!isfinite(n2)) set_status(v.ctl, MRRR_ERR_NOCONV);
+    v.W[q.wout + pos] = (nd.sigma_abs + lam_out) / q.scale;
+    v.wval[w] = lam_out;
+    v.znrm2[w] = n2;
+    if (!zc) continue;
+  }
+  if (iters) atomicAdd(&v.ctl->rq_iters, iters);
+}
+
+// One CTA per output slot: scale the column to unit norm and clear the rows
+// outside its block (problems that split).
+__global__ void k_normalize(Dev v) {
+  const int64_t nslots = v.ctl->nslots;
+  for (int64_t w = blockIdx.x; w < nslots; w += gridDim.x) {
+    const int st = v.state[w];
+    if (st != SLOT_SINGLETON && st != SLOT_FALLBACK && st != SLOT_TRIVIAL) continue;
+    const int pos = v.spos[w];
+    if (pos < 0) continue;
+    const Node& nd = v.node[v.snode[w]];
+    const Block& bk = v.blk[nd.block];
+    const Problem& q = v.prob[bk.prob];
+    double* col = v.Z + q.zout + (int64_t)pos * q.ldz;
+    const double sc = 1.0 / sqrt(v.znrm2[w]);
+    const int64_t r0 = bk.row0 - q.row0, r1 = r0 + bk.m;
+    if (q.nblocks > 1) {
+      for (int64_t i = threadIdx.x; i < q.n; i += blockDim.x)
+        col[i] = (i >= r0 && i < r1) ? col[i] * sc : 0.0;
+    } else {
+      for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) col[i] *= sc;
+    }
+  }
+}
+
+// Split problems: columns were placed by the rank of interval midpoints;
+// near-ties across blocks may leave W slightly out of order.  Odd-even
+// transposition passes (one CTA per problem) restore ascending W, moving the
+// columns of Z along.
+__global__ void k_fix_order(Dev v) {
+  __shared__ int swapped;
+  for (int64_t p = blockIdx.x; p < v.batch; p += gridDim.x) {
+    const Problem q = v.prob[p];
+    if (q.nblocks <= 1 || q.k < 2) continue;
+    double* W = v.W + q.wout;
+    int quiet = 0;
+    for (int pass = 0; pass < 2 * q.k + 2 && quiet < 2; ++pass) {
+      if (threadIdx.x == 0) swapped = 0;
+      __syncthreads();
+      const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+      for (int64_t i = (pass & 1) + 2 * (int64_t)wid; i + 1 < q.k; i += 2 * (int64_t)nw) {
+        double a = W[i], b = W[i + 1];
+        if (a > b) {
+          if (lane == 0) {
+            W[i] = b;
+            W[i + 1] = a;
+            swapped = 1;
+          }
+          if (v.Z) {
+            double* ca = v.Z + q.zout + i * q.ldz;
+            double* cb = ca + q.ldz;
+            for (int64_t r = lane; r < q.n; r += 32) {
+              double t = ca[r];
+              ca[r] = cb[r];
+              cb[r] = t;
+            }
+          }
+        }
+        __syncwarp();
+      }
+      __syncthreads();
+      quiet = swapped ? 0 : quiet + 1;
+      __syncthreads();
+    }
+  }
+}
+
+}  // namespace
+
+void launch_vectors(const Dev& v, const Grid& g, cudaStream_t s) {
+  k_vectors<<<g.vec_blocks, 128, 0, s>>>(v);
+  count_launch();
+  if (v.Z) {
+    k_normalize<<<g.nsm * 16, 256, 0, s>>>(v);
+    count_launch();
+  }
+  k_fix_order<<<g.nsm, 256, 0, s>>>(v);
+  count_launch();
+}
+
+}  // namespace mrrr

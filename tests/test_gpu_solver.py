@@ -1,0 +1,181 @@
+"""GPU parity: the CUDA MRRR solver against the CPU oracle, element by
+element, on seeded inputs of the paper's matrix families (1-2-1 / Toeplitz,
+Wilkinson, glued Wilkinson) and the workload shapes (uniform random, split
+matrices, subsets), through the C ABI."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1205_2107_gb300 import _lib, api, inputs
+from tests import checks
+
+pytestmark = pytest.mark.gpu
+
+EPS = checks.EPS
+
+
+def to_dev(x):
+    return torch.as_tensor(np.asarray(x, dtype=np.float64), device="cuda")
+
+
+def solve(d, e, il=None, iu=None, plan=None, vectors=True):
+    return api.eigh_tridiagonal(to_dev(d), to_dev(e if len(e) else np.zeros(1)), il, iu, plan=plan,
+                                vectors=vectors)
+
+
+def assert_parity(d, e, il=None, iu=None, plan=None, compare_vectors=True):
+    n = len(d)
+    il_ = 1 if il is None else il
+    iu_ = n if iu is None else iu
+    W, Z = solve(d, e, il, iu, plan)
+    Wo, Zo = oracle.eigh_tridiagonal(d, e, il_, iu_)
+    Wall = oracle.eigvalsh_tridiagonal(d, e)
+    tn = float(np.max(np.abs(Wall))) if n else 0.0
+    Wg = W.cpu().numpy()
+    assert Wg.shape == Wo.shape
+    assert np.all(np.diff(Wg) >= 0), "W not ascending"
+    err = np.max(np.abs(Wg - Wo)) if n else 0.0
+    assert err <= 4 * n * EPS * tn, f"eigenvalue error {err:.3e} > {4 * n * EPS * tn:.3e}"
+    res = float(checks.residual_cols(to_dev(d), to_dev(np.append(e, 0.0)), W, Z).max())
+    assert res <= 20 * n * EPS * tn, f"residual {res:.3e}"
+    orth = checks.orthogonality(Z)
+    assert orth <= 20 * n * EPS, f"orthogonality {orth:.3e}"
+    if compare_vectors and n > 1:
+        Zg = Z.cpu().numpy()
+        full = il_ == 1 and iu_ == n
+        for sin, bound in checks.subspace_errors(Zg, Zo, Wo if full else Wo, tn, n):
+            if full:
+                assert sin <= bound, f"subspace angle {sin:.3e} > {bound:.3e}"
+    return W, Z
+
+
+FAMILIES = {
+    "uniform": lambda n: inputs.uniform(n, 1000 + n),
+    "normal": lambda n: inputs.normal(n, 2000 + n),
+    "toeplitz": lambda n: inputs.toeplitz(n),
+    "wilkinson": lambda n: inputs.wilkinson_plus(n),
+    "clement": lambda n: inputs.clement(n),
+    "neg_definite": lambda n: (-3.0 - np.abs(inputs.uniform(n, 7)[0]), 0.3 * inputs.uniform(n, 8)[1]),
+    "repeated_d": lambda n: (np.full(n, 0.25), inputs.uniform(n, 9)[1]),
+    "zeros_in_e": lambda n: (inputs.uniform(n, 10)[0], inputs.uniform(n, 10)[1] * (np.arange(max(n - 1, 0)) % 5 != 2)),
+    "tiny_e": lambda n: (inputs.uniform(n, 11)[0], 1e-9 * inputs.uniform(n, 11)[1]),
+}
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 17, 64, 200])
+@pytest.mark.parametrize("family", sorted(FAMILIES))
+def test_small_families(family, n):
+    d, e = FAMILIES[family](n)
+    assert_parity(d, e)
+
+
+def test_uniform_1000_all():
+    d, e = inputs.uniform(1000, 1205)
+    assert_parity(d, e)
+
+
+def test_toeplitz_1000_closed_form():
+    d, e = inputs.toeplitz(1000, 2.0, -1.0)
+    W, Z = assert_parity(d, e)
+    ref = inputs.toeplitz_eigenvalues(1000, 2.0, -1.0)
+    assert np.max(np.abs(W.cpu().numpy() - ref)) <= 4 * 1000 * EPS * 4 + 16 * EPS
+    j = np.arange(1, 1001)
+    Zc = Z.cpu().numpy()
+    for k in [1, 2, 500, 999, 1000]:
+        v = np.sin(j * k * np.pi / 1001)
+        v /= np.linalg.norm(v)
+        assert abs(abs(v @ Zc[:, k - 1]) - 1) <= 1e-9
+
+
+@pytest.mark.parametrize("il,iu", [(1, 1), (1, 100), (400, 600), (1000, 1000), (37, 37), (999, 1000)])
+def test_subsets(il, iu):
+    d, e = inputs.uniform(1000, 1205)
+    assert_parity(d, e, il, iu)
+
+
+def test_glued_wilkinson_420():
+    d, e = inputs.glued_wilkinson(20)
+    assert_parity(d, e)
+
+
+@pytest.mark.parametrize("n", [201, 1001])
+def test_wilkinson_plus(n):
+    d, e = inputs.wilkinson_plus(n)
+    assert_parity(d, e)
+
+
+def test_split_all_and_subset_with_ties():
+    d1, e1 = inputs.uniform(40, 4)
+    d = np.concatenate([d1, d1, [0.5], d1[:13]])
+    e = np.concatenate([e1, [0.0], e1, [0.0], [0.0], e1[:12]])
+    assert_parity(d, e)
+    assert_parity(d, e, 10, 60)
+    assert_parity(d, e, 41, 41)
+
+
+def test_diagonal_matrix():
+    d = inputs.uniform(300, 5)[0]
+    e = np.zeros(299)
+    W, Z = assert_parity(d, e)
+    assert np.array_equal(W.cpu().numpy(), np.sort(d))
+
+
+def test_deterministic():
+    d, e = inputs.uniform(700, 3)
+    W1, Z1 = solve(d, e)
+    W2, Z2 = solve(d, e)
+    assert torch.equal(W1, W2) and torch.equal(Z1, Z2)
+
+
+def test_eigenvalues_only_matches_vectors_run():
+    d, e = inputs.uniform(500, 12)
+    W1, _ = solve(d, e)
+    W2 = solve(d, e, vectors=False)
+    Wo = oracle.eigvalsh_tridiagonal(d, e)
+    tn = np.max(np.abs(Wo))
+    assert np.max(np.abs(W2.cpu().numpy() - Wo)) <= 4 * 500 * EPS * tn
+    assert np.max(np.abs(W1.cpu().numpy() - W2.cpu().numpy())) <= 4 * 500 * EPS * tn
+
+
+# ---------------------------------------------------------------------------
+# error paths: host-side argument errors and device-side status codes
+
+
+def test_bad_arguments():
+    d = to_dev(np.ones(5))
+    e = to_dev(np.ones(4))
+    with pytest.raises(ValueError):
+        api.eigh_tridiagonal(d, e, 0, 3)
+    with pytest.raises(ValueError):
+        api.eigh_tridiagonal(d, e, 3, 6)
+    plan = api.default_plan()
+    lib = _lib.load()
+    W = torch.empty(5, dtype=torch.float64, device="cuda")
+    rc = lib.mrrr_stein(plan.handle, 5, d.data_ptr(), e.data_ptr(), 1, 5, W.data_ptr(), None, 5, None, 0, None)
+    assert rc == _lib.ERR_WORKSPACE
+    rc = lib.mrrr_stein(plan.handle, -1, d.data_ptr(), e.data_ptr(), 1, 5, W.data_ptr(), None, 5, None, 0, None)
+    assert rc == _lib.ERR_ARG
+
+
+def test_nonfinite_input_is_reported():
+    d, e = inputs.uniform(50, 1)
+    d[17] = np.nan
+    with pytest.raises(_lib.MrrrError) as ei:
+        solve(d, e)
+    assert ei.value.code == _lib.ERR_NONFINITE
+
+
+def test_bisection_cap_reports_noconv():
+    plan = api.Plan(max_bisect_steps=1)
+    d, e = inputs.uniform(100, 2)
+    with pytest.raises(_lib.MrrrError) as ei:
+        solve(d, e, plan=plan)
+    assert ei.value.code == _lib.ERR_NOCONV
+
+
+def test_tiny_pool_grows_and_succeeds():
+    plan = api.Plan(pool_rows=1, max_nodes=1)
+    d, e = inputs.wilkinson_plus(301)
+    assert_parity(d, e, plan=plan)
+    assert plan.options["pool_rows"] > 1
