@@ -63,7 +63,7 @@ typedef struct mrrr_options {
   int max_depth;           /* cluster-tree depth limit (64); deeper clusters take the
                               documented fallback and are counted in mrrr_info */
   int max_bisect_steps;    /* per interval and pass (256) */
-  int max_rq_iters;        /* Rayleigh-quotient iterations per eigenvector (12) */
+  int reserved1;
   int threads_per_block;   /* CUDA block size of the interval kernels (128) */
   int vec_blocks_per_sm;   /* resident blocks per SM of the eigenvector kernel (4) */
   int reserved0;
@@ -74,7 +74,8 @@ typedef struct mrrr_options {
                               child shift is placed, and of their refinement in the
                               child (2^-40) */
   double root_perturb;     /* relative size, in units of eps, of the seeded random
-                              perturbation of each root representation entry (4) */
+                              perturbation of each root representation entry (64,
+                              at most m/8 for a block of order m; negative = none) */
 } mrrr_options;
 
 /* Counters reported by mrrr_get_status (device values after the last solve). */
@@ -84,13 +85,13 @@ typedef struct mrrr_info {
   int64_t nodes;           /* cluster nodes created (roots excluded)        */
   int64_t pool_rows_used;  /* child-representation rows needed              */
   int64_t fallbacks;       /* eigenvalues that took the depth/shift fallback */
-  int64_t rq_iters;        /* Rayleigh-quotient iterations, all vectors     */
+  int64_t twisted_solves;  /* twisted factorizations solved, all vectors    */
   int64_t levels;          /* cluster levels processed                      */
-  int64_t diag[8];         /* event counters: [0] root-shift retries exhausted,
+  int64_t diag[12];        /* event counters: [0] root-shift retries exhausted,
                               [1] root bisection cap, [2] child bracket not
-                              confirmed, [3] child bisection cap, [4] RQ
-                              iteration cap, [5] child growth bound missed,
-                              [6] depth-limit fallbacks, [7] capacity fallbacks */
+                              confirmed, [3] child bisection cap, [4] unused,
+                              [5] child growth bound missed, [6] depth-limit
+                              fallbacks, [7] capacity fallbacks, [8]-[11] unused */
 } mrrr_info;
 
 typedef struct mrrr_plan mrrr_plan;

@@ -27,14 +27,14 @@ EXPORTS = ["mrrr_options_default", "mrrr_plan_create", "mrrr_plan_destroy", "mrr
 
 class Options(ctypes.Structure):
     _fields_ = [("gap_tol", c_double), ("classify_rtol", c_double), ("max_depth", c_int),
-                ("max_bisect_steps", c_int), ("max_rq_iters", c_int), ("threads_per_block", c_int),
+                ("max_bisect_steps", c_int), ("reserved1", c_int), ("threads_per_block", c_int),
                 ("vec_blocks_per_sm", c_int), ("reserved0", c_int), ("max_nodes", c_int64),
                 ("pool_rows", c_int64), ("cluster_rtol", c_double), ("root_perturb", c_double)]
 
 
 class Info(ctypes.Structure):
     _fields_ = [("status", c_int), ("depth", c_int), ("nodes", c_int64), ("pool_rows_used", c_int64),
-                ("fallbacks", c_int64), ("rq_iters", c_int64), ("levels", c_int64), ("diag", c_int64 * 8)]
+                ("fallbacks", c_int64), ("twisted_solves", c_int64), ("levels", c_int64), ("diag", c_int64 * 12)]
 
     def as_dict(self) -> dict:
         out = {f: getattr(self, f) for f, _ in self._fields_ if f != "diag"}

@@ -35,7 +35,7 @@ class Plan:
     """A solver plan (options + reusable device workspace) on one GPU.
 
     Options are the fields of ``mrrr_options`` (gap_tol, classify_rtol,
-    max_depth, max_bisect_steps, max_rq_iters, threads_per_block,
+    max_depth, max_bisect_steps, threads_per_block,
     vec_blocks_per_sm, max_nodes, pool_rows); zero or absent means default.
     """
 

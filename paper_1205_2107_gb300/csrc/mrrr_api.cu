@@ -75,9 +75,10 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-  size_t ctl, prob, blk, node, pool, lo, hi, gap, wval, znrm2, snode, sj, spos, state, bflag, vscr;
+  size_t ctl, prob, blk, node, pool_dl, pool_ul, chunks, lo, hi, gap, wval, znrm2, snode, sj, spos, state, bflag,
+      vscr;
   size_t total;
-  int64_t max_blocks, max_nodes, max_slots, pool_rows, vscr_threads, vscr_rows;
+  int64_t max_blocks, max_nodes, max_slots, pool_rows, vscr_threads, vscr_rows, max_chunks;
 };
 
 int vec_threads(const mrrr_plan* p) { return p->nsm * std::max(1, p->opt.vec_blocks_per_sm) * 128; }
@@ -110,7 +111,11 @@ Layout make_layout(const mrrr_plan* p, int batch, int64_t n_total, int64_t k_tot
   L.prob = take(sizeof(Problem) * (size_t)std::max(batch, 1));
   L.blk = take(sizeof(Block) * (size_t)L.max_blocks);
   L.node = take(sizeof(Node) * (size_t)L.max_nodes);
-  L.pool = take(sizeof(RepRow) * (size_t)L.pool_rows);
+  L.pool_dl = take(sizeof(double2) * (size_t)L.pool_rows);
+  L.pool_ul = take(sizeof(double2) * (size_t)L.pool_rows);
+  L.max_chunks = engine_max_chunks(L.max_slots, L.max_nodes);
+  L.chunks = take(sizeof(Chunk) * (size_t)L.max_chunks);
+
   L.lo = take(sizeof(double) * (size_t)L.max_slots);
   L.hi = take(sizeof(double) * (size_t)L.max_slots);
   L.gap = take(sizeof(double) * (size_t)L.max_slots);
@@ -121,7 +126,7 @@ Layout make_layout(const mrrr_plan* p, int batch, int64_t n_total, int64_t k_tot
   L.spos = take(sizeof(int) * (size_t)L.max_slots);
   L.state = take(sizeof(int) * (size_t)L.max_slots);
   L.bflag = take((size_t)L.max_slots);
-  L.vscr = take(sizeof(double) * 2 * (size_t)L.vscr_threads * (size_t)L.vscr_rows);
+  L.vscr = take(sizeof(double) * (size_t)L.vscr_threads * (size_t)L.vscr_rows);
   L.total = off;
   return L;
 }
@@ -134,7 +139,11 @@ Dev make_dev(const mrrr_plan* p, const Layout& L, void* ws, int batch, const dou
   v.prob = reinterpret_cast<Problem*>(b + L.prob);
   v.blk = reinterpret_cast<Block*>(b + L.blk);
   v.node = reinterpret_cast<Node*>(b + L.node);
-  v.pool = reinterpret_cast<RepRow*>(b + L.pool);
+  v.rep_dl = reinterpret_cast<double2*>(b + L.pool_dl);
+  v.rep_ul = reinterpret_cast<double2*>(b + L.pool_ul);
+  v.chunks = reinterpret_cast<Chunk*>(b + L.chunks);
+
+  v.max_chunks = L.max_chunks;
   v.pool_cap = L.pool_rows;
   v.max_blocks = (int)std::min<int64_t>(L.max_blocks, INT32_MAX);
   v.max_nodes = (int)L.max_nodes;
@@ -165,7 +174,6 @@ Dev make_dev(const mrrr_plan* p, const Layout& L, void* ws, int batch, const dou
   v.root_perturb = o.root_perturb;
   v.max_depth = o.max_depth;
   v.max_bisect = o.max_bisect_steps;
-  v.max_rq = o.max_rq_iters;
   return v;
 }
 
@@ -210,6 +218,8 @@ mrrr_status solve(mrrr_plan* p, const ProblemArgs& a, const double* d, const dou
     if (p->host_ctl->level_new == 0) break;
     launch_level_children(v, level, g, s);
   }
+  launch_engine(v, 3, g, s);
+  tm->mark("final_bisect", s);
   launch_vectors(v, g, s);
   tm->mark("vectors", s);
   tm->finish();
@@ -233,11 +243,10 @@ mrrr_status mrrr_options_default(mrrr_options* opt) {
   opt->classify_rtol = 0x1p-20;
   opt->max_depth = 64;
   opt->max_bisect_steps = 256;
-  opt->max_rq_iters = 12;
   opt->threads_per_block = 128;
   opt->vec_blocks_per_sm = 1;
   opt->cluster_rtol = 0x1p-40;
-  opt->root_perturb = 4.0;
+  opt->root_perturb = 64.0;
   return MRRR_OK;
 }
 
@@ -251,7 +260,6 @@ mrrr_status mrrr_plan_create(mrrr_plan** plan, const mrrr_options* opt) {
     if (opt->classify_rtol > 0) o.classify_rtol = opt->classify_rtol;
     if (opt->max_depth > 0) o.max_depth = opt->max_depth;
     if (opt->max_bisect_steps > 0) o.max_bisect_steps = opt->max_bisect_steps;
-    if (opt->max_rq_iters > 0) o.max_rq_iters = opt->max_rq_iters;
     if (opt->threads_per_block > 0) o.threads_per_block = opt->threads_per_block;
     if (opt->vec_blocks_per_sm > 0) o.vec_blocks_per_sm = opt->vec_blocks_per_sm;
     if (opt->max_nodes > 0) o.max_nodes = opt->max_nodes;
@@ -345,9 +353,9 @@ mrrr_status mrrr_get_status(mrrr_plan* plan, mrrr_stream stream, mrrr_info* out)
     out->nodes = (int64_t)c.nodes - c.nblocks;
     out->pool_rows_used = c.pool_need;
     out->fallbacks = (int64_t)c.fallbacks;
-    out->rq_iters = (int64_t)c.rq_iters;
+    out->twisted_solves = (int64_t)c.twisted_solves;
     out->levels = c.levels;
-    for (int i = 0; i < 8; ++i) out->diag[i] = (int64_t)c.diag[i];
+    for (int i = 0; i < 12; ++i) out->diag[i] = (int64_t)c.diag[i];
   }
   return static_cast<mrrr_status>(c.status);
 }

@@ -3,10 +3,11 @@
 //
 // Notation follows the paper's Sec. 3.1.1: a representation (RRR) of a
 // shifted block is L D L^T with L unit lower bidiagonal (subdiagonal l_i) and
-// D diagonal.  Each row i of a representation stores
-//   D_i, LLD_i = l_i^2 D_i, l_i, LD_i = l_i D_i          (32 bytes, RepRow)
-// so that the Sturm count (D, LLD), the stationary and progressive qd
-// transforms (D, l, LD, LLD) read one contiguous record per row.
+// D diagonal.  A representation of m rows is stored as two planes of
+// 16-byte records in the representation pool:
+//   dl[i] = (D_i, LLD_i = l_i^2 D_i)   -- all a Sturm count reads
+//   ul[i] = (l_i, LD_i = l_i D_i)      -- the rest of the qd transforms
+// so a Sturm count streams exactly 16 bytes per row into shared memory.
 #pragma once
 
 #include <cstdint>
@@ -26,6 +27,12 @@ enum : int {
   SLOT_TRIVIAL = 3,    // 1x1 block: eigenvalue d, vector e_row
   SLOT_FALLBACK = 4,   // cluster beyond the depth limit, treated as singleton
 };
+
+
+__device__ __forceinline__ bool slot_final(int st) {
+  return st == SLOT_SINGLETON || st == SLOT_FALLBACK;
+}
+
 
 struct Problem {
   int64_t row0;   // first row in the packed d / e
@@ -66,8 +73,15 @@ struct Node {
   double spdiam;        // width of the block's spectrum (shift invariant)
 };
 
-struct RepRow {
+struct RepRow {  // one row of a representation, unpacked
   double D, LLD, l, LD;
+};
+
+// Chunk of the interval engine: slots s0..s1-1 of one node.
+struct Chunk {
+  int node;
+  int pad_;
+  int64_t s0, s1;
 };
 
 // Device control block (first bytes of the workspace).
@@ -82,10 +96,17 @@ struct Ctl {
   int64_t pool_top;       // rows of the pool in use (roots + children)
   int64_t pool_need;      // rows requested (may exceed the capacity)
   unsigned long long fallbacks;
-  unsigned long long rq_iters;
+  unsigned long long twisted_solves;
   int levels;
   int pad_;
-  unsigned long long diag[8];  // per-site event counters (see mrrr_info.diag)
+  unsigned long long diag[12];  // per-site event counters (see mrrr_info.diag)
+  int nchunks;            // big (CTA) chunks of the current engine launch
+  int chunk_next;         // dynamic counter over big chunks
+  int nsmall;             // small (warp) chunks, stored from the end of the list
+  int small_next;         // dynamic counter over small chunks
+  long long big_slots;    // slots in big nodes (sizes the big chunks)
+  int pad2_;
+  int pad3_;
 };
 
 // Indices of Ctl::diag (mirrored in mrrr_info.diag).
@@ -94,10 +115,14 @@ enum : int {
   DIAG_ROOT_BISECT = 1,    // root bisection hit its step cap (intervals)
   DIAG_REFINE_BRACKET = 2, // child bracket could not be confirmed (intervals)
   DIAG_REFINE_BISECT = 3,  // child bisection hit its step cap (intervals)
-  DIAG_RQ = 4,             // Rayleigh-quotient iteration cap (vectors)
+  DIAG_SPARE4 = 4,
   DIAG_CHILD_GROWTH = 5,   // no child shift met the growth bound (clusters)
   DIAG_DEPTH = 6,          // depth-limit fallback (eigenvalues)
   DIAG_CAPACITY = 7,       // node table / pool full fallback (eigenvalues)
+  DIAG_SPARE8 = 8,
+  DIAG_SPARE9 = 9,
+  DIAG_SPARE10 = 10,
+  DIAG_SPARE11 = 11,
 };
 
 // Device views of the workspace, passed by value to kernels.
@@ -106,8 +131,12 @@ struct Dev {
   Problem* prob;
   Block* blk;
   Node* node;
-  RepRow* pool;
+  double2* rep_dl;    // (D, LLD) plane of the representation pool
+  double2* rep_ul;    // (l, LD) plane
   int64_t pool_cap;   // rows
+  Chunk* chunks;      // work list of the interval engine
+  int64_t max_chunks;
+
   int max_blocks;
   int max_nodes;
   int64_t max_slots;
@@ -140,7 +169,6 @@ struct Dev {
   double root_perturb;  // root perturbation size in ulps
   int max_depth;
   int max_bisect;
-  int max_rq;
 };
 
 __device__ __forceinline__ void set_status(Ctl* c, int code) {
@@ -151,6 +179,26 @@ __device__ __forceinline__ void diag(Ctl* c, int site, unsigned long long k = 1)
   atomicAdd(&c->diag[site], k);
 }
 
+__device__ __forceinline__ RepRow rep_row(const double2* __restrict__ dl, const double2* __restrict__ ul, int64_t i) {
+  const double2 a = dl[i], b = ul[i];
+  return RepRow{a.x, a.y, b.x, b.y};
+}
+__device__ __forceinline__ void rep_store(double2* dl, double2* ul, int64_t i, const RepRow& r) {
+  dl[i] = make_double2(r.D, r.LLD);
+  ul[i] = make_double2(r.l, r.LD);
+}
+
+// Zero-pivot guard of a representation whose entries are bounded by R (the
+// problem is scaled so that G(T) is in [1,2)): pivots below pivmin are
+// replaced by -pivmin.  pivmin = 2^-900 max(1, R)^2 keeps every quotient of
+// the Sturm recurrence finite; as an exponent field for the integer test of
+// the division-free count.
+__device__ __forceinline__ double pivmin_for(double R) {
+  double r = fmin(fmax(R, 1.0), 0x1p60);
+  return 0x1p-900 * r * r;
+}
+__device__ __forceinline__ int exp_field(double x) { return (__double2hiint(x) >> 20) & 0x7ff; }
+
 // ---------------------------------------------------------------------------
 // Sturm count on a representation (Sec. 3.1.1: bisection on the RRR).  The
 // number of negative pivots D+_i of the stationary transform
@@ -158,25 +206,45 @@ __device__ __forceinline__ void diag(Ctl* c, int site, unsigned long long k = 1)
 //   s_1 = -tau,  D+_i = D_i + s_i,  s_{i+1} = LLD_i s_i / D+_i - tau,
 // equals the number of eigenvalues of L D L^T below tau (Sylvester's law of
 // inertia).  Pivots with |D+_i| < pivmin are replaced by -pivmin.
-__device__ __forceinline__ int negcount_div(const RepRow* __restrict__ rep, int m, double tau,
-                                            double pivmin) {
-  int cnt = 0;
-  double s = -tau;
-  for (int i = 0; i < m - 1; ++i) {
-    const double2 dl = *reinterpret_cast<const double2*>(&rep[i].D);  // D, LLD
-    double dp = dl.x + s;
-    if (fabs(dp) < pivmin) dp = -pivmin;
-    cnt += (dp < 0.0);
-    s = fma(dl.y, s / dp, -tau);
+//
+// Division-free form used by the kernels: with s_i = a/b,
+//   c = D_i b + a            (= D+_i b; sign(D+_i) = sign(c) sign(b))
+//   a' = LLD_i a - tau c,  b' = c          (so s_{i+1} = a'/b')
+// and (a', b') rescaled by the power of two that brings |b'| into [1,2)
+// (integer operations on the exponent field; a' flushes to 0 below the
+// normal range).  Three FP64 operations per row instead of a division; the
+// rounding differs from the quotient form by a relative perturbation of tau
+// of one ulp per row, i.e. a diagonal perturbation of size eps|tau| (so the
+// count keeps the relative accuracy of the representation).
+__device__ __forceinline__ void count_step(double D, double LLD, double tau, int pivexp, double pivmin,
+                                           double& a, double& b, int& neg) {
+  double c = fma(D, b, a);
+  int chi = __double2hiint(c);
+  const int bhi = __double2hiint(b);
+  int cexp = (chi >> 20) & 0x7ff;
+  if (cexp < pivexp) {  // |D+| < pivmin (|b| in [1,2)): counts as negative
+    c = bhi < 0 ? pivmin : -pivmin;
+    chi = __double2hiint(c);
+    cexp = pivexp;
   }
-  double dp = rep[m - 1].D + s;
-  if (fabs(dp) < pivmin) dp = -pivmin;
-  cnt += (dp < 0.0);
-  return cnt;
+  neg += (chi ^ bhi) < 0;
+  const double an = fma(LLD, a, -tau * c);
+  const int k = cexp - 1023;
+  b = __hiloint2double((chi & 0x800fffff) | 0x3ff00000, __double2loint(c));
+  const int ahi = __double2hiint(an);
+  const int aexp = (ahi >> 20) & 0x7ff;
+  a = (aexp - k <= 0) ? 0.0 : __hiloint2double(ahi - (k << 20), __double2loint(an));
 }
 
-__device__ __forceinline__ int negcount(const RepRow* __restrict__ rep, int m, double tau, double pivmin) {
-  return negcount_div(rep, m, tau, pivmin);
+__device__ __forceinline__ int negcount(const double2* __restrict__ dl, int m, double tau, double pivmin) {
+  const int pivexp = exp_field(pivmin);
+  double a = -tau, b = 1.0;
+  int neg = 0;
+  for (int i = 0; i < m; ++i) {
+    const double2 r = dl[i];
+    count_step(r.x, r.y, tau, pivexp, pivmin, a, b, neg);
+  }
+  return neg;
 }
 
 __device__ __forceinline__ bool converged(double lo, double hi, double rtol, double atol) {
@@ -186,20 +254,64 @@ __device__ __forceinline__ bool converged(double lo, double hi, double rtol, dou
 
 // Bisection of [lo, hi] (count(lo) <= j-1 < count(hi) on entry) until the
 // width is below rtol relative (atol absolute).  Returns steps taken.
-__device__ __forceinline__ int bisect_interval(const RepRow* __restrict__ rep, int m, int j,
-                                               double pivmin, double rtol, double atol, int maxit,
-                                               double& lo, double& hi) {
+__device__ __forceinline__ int bisect_interval(const double2* __restrict__ dl, int m, int j, double pivmin,
+                                               double rtol, double atol, int maxit, double& lo, double& hi) {
   int it = 0;
   for (; it < maxit; ++it) {
     if (converged(lo, hi, rtol, atol)) break;
     double mid = 0.5 * (lo + hi);
     if (mid <= lo || mid >= hi) break;
-    if (negcount(rep, m, mid, pivmin) >= j)
+    if (negcount(dl, m, mid, pivmin) >= j)
       hi = mid;
     else
       lo = mid;
   }
   return it;
+}
+
+// ---------------------------------------------------------------------------
+// Bulk asynchronous copies into shared memory (TMA, cp.async.bulk) completed
+// on an mbarrier, with bounded waits.
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for phase `parity` of bar; gives up after a bounded number of polls
+// (returns false).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (int it = 0; it < (1 << 22); ++it) {
+    if (mbar_test(bar, parity)) return true;
+    if (it > 64) __nanosleep(64);
+  }
+  return false;
 }
 
 // Grid helpers

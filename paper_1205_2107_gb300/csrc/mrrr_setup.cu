@@ -1,7 +1,7 @@
 // mrrr_setup.cu -- problem table, norm and scaling, splitting into blocks,
-// root representations and root bisection (paper Sec. 3.1.1: "At first, a
-// representation RRR0 is chosen ... As a second step, bisection is used to
-// compute approximations to each eigenvalue"; splitting follows the footnote
+// root representations and root bisection (Sec. 3.1.1: first a root
+// representation RRR0 of the shifted matrix, then bisection for an
+// approximation of every wanted eigenvalue; splitting follows the footnote
 // on numerical irreducibility: off-diagonals below eps*||T|| are zero).
 #include <cmath>
 
@@ -11,7 +11,7 @@ namespace mrrr {
 
 namespace {
 
-constexpr double kPivmin = 0x1p-982;  // zero-pivot guard for scaled problems
+constexpr double kPivmin = 0x1p-900;  // zero-pivot guard while the root is built
 
 // splitmix64 (Steele, Lea and Flood, "Fast splittable pseudorandom number
 // generators", OOPSLA 2014): a counter-based 64-bit mixing function.
@@ -258,13 +258,6 @@ __global__ void k_blocks(Dev v) {
   }
 }
 
-// ---------------------------------------------------------------------------
-// Sturm count on the scaled T of a block (used only to verify the root
-// bracket): q_1 = d_1 - x, q_i = d_i - x - e_{i-1}^2 / q_{i-1}.
-__device__ int count_rep_bracket(const RepRow* rep, int m, double x) {
-  return negcount(rep, m, x, kPivmin);
-}
-
 // One thread per block: Gershgorin bounds, root shift sigma at the end of the
 // spectrum nearer the wanted indices, L0 D0 L0^T = T - sigma I (definite),
 // retried with sigma pushed outward until every pivot has the right sign.
@@ -275,7 +268,8 @@ __global__ void k_root(Dev v) {
     const Problem q = v.prob[bk.prob];
     const int m = bk.m;
     const int64_t lr0 = bk.row0 - q.row0;  // local row of the block start
-    RepRow* rep = v.pool + bk.row0;
+    double2* dl = v.rep_dl + bk.row0;
+    double2* ul = v.rep_ul + bk.row0;
     Node nd;
     nd.block = (int)b;
     nd.depth = 0;
@@ -289,7 +283,7 @@ __global__ void k_root(Dev v) {
     nd.pivmin = kPivmin;
     if (m == 1) {
       double d0 = scaled_d(v, q, lr0);
-      rep[0] = RepRow{0.0, 0.0, 0.0, 0.0};
+      rep_store(dl, ul, 0, RepRow{0.0, 0.0, 0.0, 0.0});
       nd.sigma_rel = nd.sigma_abs = d0;
       nd.spdiam = 0.0;
       bk.gl = bk.gu = 0.0;
@@ -327,11 +321,11 @@ __global__ void k_root(Dev v) {
         double l = ei / Dcur;
         double LD = l * Dcur;
         double LLD = l * LD;
-        rep[i] = RepRow{Dcur, LLD, l, LD};
+        rep_store(dl, ul, i, RepRow{Dcur, LLD, l, LD});
         Dcur = (scaled_d(v, q, lr0 + i + 1) - sigma) - LLD;
       }
       if (ok && (!(left ? Dcur > kPivmin : Dcur < -kPivmin) || !isfinite(Dcur))) ok = false;
-      if (ok) rep[m - 1] = RepRow{Dcur, 0.0, 0.0, 0.0};
+      if (ok) rep_store(dl, ul, m - 1, RepRow{Dcur, 0.0, 0.0, 0.0});
     }
     if (!ok) {
       set_status(v.ctl, MRRR_ERR_NOCONV);
@@ -343,54 +337,38 @@ __global__ void k_root(Dev v) {
     // coincidence of eigenvalues of identical glued blocks (Dhillon, Parlett
     // and Voemel, "Glued matrices and the MRRR algorithm", 2005).
     if (v.root_perturb > 0.0) {
-      // small blocks get proportionally less (the eigenvalue budget 4 m eps ||T||
-      // is tight there, and glued copies only matter for large blocks)
-      const double amp = v.root_perturb * kEps * fmin(1.0, m / 32.0);
+      // at most m/8 ulps: the eigenvalue budget 4 m eps ||T|| is tight for
+      // small blocks, and glued copies only matter for large ones
+      const double amp = fmin(v.root_perturb, m / 8.0) * kEps;
       for (int i = 0; i < m; ++i) {
         const uint64_t row = (uint64_t)(bk.row0 + i);
         double u1 = uniform_pm1(splitmix64(2 * row));
         double u2 = uniform_pm1(splitmix64(2 * row + 1));
-        RepRow r = rep[i];
+        RepRow r = rep_row(dl, ul, i);
         r.D *= 1.0 + amp * u1;
         r.l *= 1.0 + amp * u2;
         r.LD = r.l * r.D;
         r.LLD = r.l * r.LD;
-        rep[i] = r;
+        rep_store(dl, ul, i, r);
       }
     }
+    double R = 0.0;
+    for (int i = 0; i < m; ++i) {
+      const double2 x = dl[i];
+      R = fmax(R, fmax(fabs(x.x), fabs(x.y)));
+    }
+    nd.pivmin = pivmin_for(R);
     // initial bracket in root coordinates, checked with Sturm counts
     double pad = 4.0 * kEps * m * (gmax + spdiam) + 4.0 * kPivmin;
     double lo = gl - sigma - pad, hi = gu - sigma + pad;
-    for (int t = 0; t < 60 && count_rep_bracket(rep, m, lo) > 0; ++t) lo -= (hi - lo);
-    for (int t = 0; t < 60 && count_rep_bracket(rep, m, hi) < m; ++t) hi += (hi - lo);
+    for (int t = 0; t < 60 && negcount(dl, m, lo, nd.pivmin) > 0; ++t) lo -= (hi - lo);
+    for (int t = 0; t < 60 && negcount(dl, m, hi, nd.pivmin) < m; ++t) hi += (hi - lo);
     bk.gl = lo;
     bk.gu = hi;
     nd.sigma_rel = nd.sigma_abs = sigma;
     nd.spdiam = spdiam;
     v.blk[b] = bk;
     v.node[b] = nd;
-  }
-}
-
-// ---------------------------------------------------------------------------
-// One thread per slot: bisection on the root representation to the
-// classification accuracy (relative width rtol).
-__global__ void k_bisect_root(Dev v) {
-  const int64_t nslots = v.ctl->nslots;
-  for (int64_t w = gtid(); w < nslots; w += gstride()) {
-    if (v.state[w] != SLOT_ACTIVE) continue;
-    const int b = v.snode[w];
-    const Block bk = v.blk[b];
-    const Node nd = v.node[b];
-    const RepRow* rep = v.pool + nd.rep;
-    double lo = bk.gl, hi = bk.gu;
-    int it = bisect_interval(rep, bk.m, v.sj[w], nd.pivmin, v.rtol, 4.0 * nd.pivmin, v.max_bisect, lo, hi);
-    if (it >= v.max_bisect) {
-      set_status(v.ctl, MRRR_ERR_NOCONV);
-      diag(v.ctl, DIAG_ROOT_BISECT);
-    }
-    v.lo[w] = lo;
-    v.hi[w] = hi;
   }
 }
 
@@ -437,8 +415,7 @@ void launch_setup(const Dev& v, const ProblemArgs& a, int64_t n_total, const Gri
   k_root<<<std::max(pb, 1), 128, 0, s>>>(v);
   count_launch();
   mark_stage("root", s);
-  k_bisect_root<<<g.slot_blocks, g.tpb, 0, s>>>(v);
-  count_launch();
+  launch_engine(v, 0, g, s);
   mark_stage("bisect_root", s);
   k_rank<<<g.slot_blocks, g.tpb, 0, s>>>(v);
   count_launch();

@@ -97,153 +97,121 @@ __global__ void k_classify_runs(Dev v, int level) {
   }
 }
 
-// One thread per slot of a new cluster: refine its interval in the PARENT's
-// representation to the cluster accuracy, so that the child shift can be
-// placed right at the cluster's end.
-__global__ void k_prerefine(Dev v) {
-  const int begin = v.ctl->level_begin;
-  const int64_t nslots = v.ctl->nslots;
-  for (int64_t w = gtid(); w < nslots; w += gstride()) {
-    if (v.state[w] != SLOT_ACTIVE) continue;
-    const int nid = v.snode[w];
-    if (nid < begin) continue;
-    const Node c = v.node[nid];
-    const Node p = v.node[c.parent];
-    const int m = v.blk[c.block].m;
-    double lo = v.lo[w], hi = v.hi[w];
-    int it = bisect_interval(v.pool + p.rep, m, v.sj[w], p.pivmin, v.rtol_cluster, 4.0 * p.pivmin,
-                             v.max_bisect, lo, hi);
-    if (it >= v.max_bisect) {
-      set_status(v.ctl, MRRR_ERR_NOCONV);
-      diag(v.ctl, DIAG_REFINE_BISECT);
-    }
-    v.lo[w] = lo;
-    v.hi[w] = hi;
-  }
-}
-
 // Stationary qd transform (dstqds) of the parent representation with shift
-// sigma, written as the child representation:
+// sigma (paper Sec. 3.1.1: Lc Dc Lc^T = L D L^T - sigma_c I, computed in a
+// mixed relatively stable way):
 //   s_1 = -sigma, D+_i = D_i + s_i, L+_i = LD_i / D+_i,
 //   s_{i+1} = L+_i l_i s_i - sigma.
-// Returns max |D+_i| (infinite when a pivot is not finite).
-__device__ double dstqds_child(const RepRow* __restrict__ par, RepRow* __restrict__ out, int m,
-                               double sigma, double pivmin) {
+// growth_only: returns max |D+_i| without storing (infinite when a pivot is
+// not finite); otherwise writes the child rows and returns
+// max(|D+_i|, |LLD+_i|).
+template <bool kStore>
+__device__ double dstqds_child(const double2* __restrict__ pdl, const double2* __restrict__ pul,
+                               double2* __restrict__ cdl, double2* __restrict__ cul, int m, double sigma,
+                               double pivmin) {
   double s = -sigma;
   double growth = 0.0;
   for (int i = 0; i < m - 1; ++i) {
-    const RepRow r = par[i];
+    const RepRow r = rep_row(pdl, pul, i);
     double dp = r.D + s;
     if (fabs(dp) < pivmin) dp = -pivmin;
-    double lp = r.LD / dp;
+    const double lp = r.LD / dp;
     s = fma(lp, r.l * s, -sigma);
-    double ldp = lp * dp;
-    out[i] = RepRow{dp, lp * ldp, lp, ldp};
     growth = fmax(growth, fabs(dp));
+    if (kStore) {
+      const double ldp = lp * dp;
+      const double lldp = lp * ldp;
+      rep_store(cdl, cul, i, RepRow{dp, lldp, lp, ldp});
+      growth = fmax(growth, fabs(lldp));
+    }
   }
-  double dp = par[m - 1].D + s;
+  double dp = pdl[m - 1].x + s;
   if (fabs(dp) < pivmin) dp = -pivmin;
-  out[m - 1] = RepRow{dp, 0.0, 0.0, 0.0};
+  if (kStore) rep_store(cdl, cul, m - 1, RepRow{dp, 0.0, 0.0, 0.0});
   growth = fmax(growth, fabs(dp));
   if (!isfinite(growth)) growth = INFINITY;
   return growth;
 }
 
-// One thread per new node: choose sigma_c at the left or right end of the
-// cluster, moved outward geometrically until the element growth
-// max|D+| <= 8 * spdiam; if no candidate qualifies the smallest growth seen
-// is kept and the cluster is counted as a fallback.
+constexpr int kShiftTries = 10;  // per side
+
+// One warp per new node: the lanes evaluate 2 x kShiftTries candidate
+// shifts at once -- the left end lo_f - delta_t and the right end
+// hi_l + delta_t of the cluster, delta_t = 4 eps |end| 4^t -- and the first
+// candidate (in the order t = 0, 1, ..., left before right) whose element
+// growth max|D+| is at most 8 spdiam is taken; if none is, the candidate with
+// the smallest growth (counted in the diagnostics).  The chosen transform is
+// then recomputed with stores into rows of the representation pool.
 __global__ void k_childrep(Dev v) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = gtid() >> 5, nwarps = gstride() >> 5;
   const int begin = v.ctl->level_begin;
   const int end = min(v.ctl->nodes, v.max_nodes);
-  for (int64_t id = begin + gtid(); id < end; id += gstride()) {
+  for (int64_t id = begin + warp; id < end; id += nwarps) {
     Node c = v.node[id];
     const Node p = v.node[c.parent];
     const int m = v.blk[c.block].m;
-    int64_t base = atomicAdd((unsigned long long*)&v.ctl->pool_top, (unsigned long long)m);
-    atomicMax((unsigned long long*)&v.ctl->pool_need, (unsigned long long)(base + m));
+    int64_t base = 0;
+    if (lane == 0) {
+      base = (int64_t)atomicAdd((unsigned long long*)&v.ctl->pool_top, (unsigned long long)m);
+      atomicMax((unsigned long long*)&v.ctl->pool_need, (unsigned long long)(base + m));
+    }
+    base = __shfl_sync(0xffffffffu, base, 0);
     if (base + m > v.pool_cap) {
       set_status(v.ctl, MRRR_ERR_QUEUE);
       // vectors of these slots are taken at the parent node
-      for (int64_t t = c.first; t <= c.last; ++t) {
+      for (int64_t t = c.first + lane; t <= c.last; t += 32) {
         v.state[t] = SLOT_FALLBACK;
         v.snode[t] = c.parent;
         double a = (t == c.first) ? c.gapl : v.lo[t] - v.hi[t - 1];
         double b = (t == c.last) ? c.gapr : v.lo[t + 1] - v.hi[t];
         v.gap[t] = fmax(fmin(a, b), 0.0);
       }
-      atomicAdd(&v.ctl->fallbacks, (unsigned long long)(c.last - c.first + 1));
-      diag(v.ctl, DIAG_CAPACITY, (unsigned long long)(c.last - c.first + 1));
-      c.rep = p.rep;
-      c.depth = -1;  // inert
-      v.node[id] = c;
+      if (lane == 0) {
+        atomicAdd(&v.ctl->fallbacks, (unsigned long long)(c.last - c.first + 1));
+        diag(v.ctl, DIAG_CAPACITY, (unsigned long long)(c.last - c.first + 1));
+        c.rep = -1;
+        c.depth = -1;  // inert
+        v.node[id] = c;
+      }
       continue;
     }
-    const RepRow* par = v.pool + p.rep;
-    RepRow* out = v.pool + base;
+    const double2* pdl = v.rep_dl + p.rep;
+    const double2* pul = v.rep_ul + p.rep;
     const double lo_f = v.lo[c.first], hi_l = v.hi[c.last];
     const double bound = 8.0 * c.spdiam;
-    double best_g = INFINITY, best_sigma = lo_f;
-    double sigma = lo_f;
-    bool ok = false;
-    for (int t = 0; t < 10 && !ok; ++t) {
-      for (int side = 0; side < 2 && !ok; ++side) {
-        double ref = side == 0 ? lo_f : hi_l;
-        double delta = 4.0 * kEps * fabs(ref) * (double)(1LL << (2 * t)) + 4.0 * c.pivmin;
-        sigma = side == 0 ? lo_f - delta : hi_l + delta;
-        double g = dstqds_child(par, out, m, sigma, c.pivmin);
-        if (g < best_g) best_g = g, best_sigma = sigma;
-        ok = g <= bound;
+    double sigma = lo_f, g = INFINITY;
+    if (lane < 2 * kShiftTries) {
+      const int side = lane & 1, t = lane >> 1;
+      const double ref = side == 0 ? lo_f : hi_l;
+      const double delta = 4.0 * kEps * fabs(ref) * (double)(1LL << (2 * t)) + 4.0 * p.pivmin;
+      sigma = side == 0 ? lo_f - delta : hi_l + delta;
+      g = dstqds_child<false>(pdl, pul, nullptr, nullptr, m, sigma, p.pivmin);
+    }
+    const unsigned okmask = __ballot_sync(0xffffffffu, g <= bound);
+    int pick;
+    if (okmask) {
+      pick = __ffs(okmask) - 1;
+    } else {  // smallest growth, lowest lane on ties
+      double bg = g;
+      int bl = lane;
+      for (int o = 16; o; o >>= 1) {
+        double og = __shfl_xor_sync(0xffffffffu, bg, o);
+        int ol = __shfl_xor_sync(0xffffffffu, bl, o);
+        if (og < bg || (og == bg && ol < bl)) bg = og, bl = ol;
       }
+      pick = bl;
+      if (lane == 0) diag(v.ctl, DIAG_CHILD_GROWTH);
     }
-    if (!ok) {
-      sigma = best_sigma;
-      dstqds_child(par, out, m, sigma, c.pivmin);
-      diag(v.ctl, DIAG_CHILD_GROWTH);
+    sigma = __shfl_sync(0xffffffffu, sigma, pick);
+    if (lane == 0) {
+      const double R = dstqds_child<true>(pdl, pul, v.rep_dl + base, v.rep_ul + base, m, sigma, p.pivmin);
+      c.rep = base;
+      c.sigma_rel = sigma;
+      c.sigma_abs = p.sigma_abs + sigma;
+      c.pivmin = pivmin_for(R);
+      v.node[id] = c;
     }
-    c.rep = base;
-    c.sigma_rel = sigma;
-    c.sigma_abs = p.sigma_abs + sigma;
-    v.node[id] = c;
-  }
-}
-
-// One thread per slot of a new node: move its interval into the child's
-// coordinates, widen it until Sturm counts on the child confirm the bracket,
-// then bisect to the classification accuracy.
-__global__ void k_refine(Dev v) {
-  const int begin = v.ctl->level_begin;
-  const int64_t nslots = v.ctl->nslots;
-  for (int64_t w = gtid(); w < nslots; w += gstride()) {
-    if (v.state[w] != SLOT_ACTIVE) continue;
-    const int nid = v.snode[w];
-    if (nid < begin) continue;
-    const Node c = v.node[nid];
-    if (c.depth < 0) continue;
-    const int m = v.blk[c.block].m;
-    const RepRow* rep = v.pool + c.rep;
-    const int j = v.sj[w];
-    const double plo = v.lo[w], phi = v.hi[w];
-    double delta = 16.0 * kEps * fmax(fabs(plo), fabs(phi)) + 4.0 * c.pivmin;
-    double lo = 0.0, hi = 0.0;
-    bool ok = false;
-    for (int t = 0; t < 24 && !ok; ++t) {
-      lo = (plo - c.sigma_rel) - delta;
-      hi = (phi - c.sigma_rel) + delta;
-      ok = negcount(rep, m, lo, c.pivmin) <= j - 1 && negcount(rep, m, hi, c.pivmin) >= j;
-      delta *= 4.0;
-    }
-    if (!ok) {
-      set_status(v.ctl, MRRR_ERR_NOCONV);
-      diag(v.ctl, DIAG_REFINE_BRACKET);
-    }
-    int it = bisect_interval(rep, m, j, c.pivmin, v.rtol_cluster, 4.0 * c.pivmin, v.max_bisect, lo, hi);
-    if (it >= v.max_bisect) {
-      set_status(v.ctl, MRRR_ERR_NOCONV);
-      diag(v.ctl, DIAG_REFINE_BISECT);
-    }
-    v.lo[w] = lo;
-    v.hi[w] = hi;
   }
 }
 
@@ -260,14 +228,12 @@ void launch_level_classify(const Dev& v, int level, const Grid& g, cudaStream_t 
 
 void launch_level_children(const Dev& v, int level, const Grid& g, cudaStream_t s) {
   (void)level;
-  k_prerefine<<<g.slot_blocks, g.tpb, 0, s>>>(v);
-  count_launch();
+  launch_engine(v, 1, g, s);
   mark_stage("prerefine", s);
-  k_childrep<<<g.slot_blocks, 32, 0, s>>>(v);
+  k_childrep<<<g.slot_blocks, 128, 0, s>>>(v);
   count_launch();
   mark_stage("childrep", s);
-  k_refine<<<g.slot_blocks, g.tpb, 0, s>>>(v);
-  count_launch();
+  launch_engine(v, 2, g, s);
   mark_stage("refine", s);
 }
 

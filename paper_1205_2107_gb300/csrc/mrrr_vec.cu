@@ -1,8 +1,11 @@
-// mrrr_vec.cu -- eigenvectors of singletons by one twisted factorization per
-// Rayleigh-quotient step (paper Sec. 3.1.1, Eq. errorangle: "one step of
-// inverse iteration with a twisted factorization" on the node's RRR), the
-// normalisation of the columns of Z, and the ordering of split problems.
+// mrrr_vec.cu -- eigenvectors of singletons by one twisted factorization each
+// on the node's representation (Sec. 3.1.1: a singleton's vector is computed
+// in isolation from its representation, with the error bound of the
+// eigenvector-angle inequality), the normalisation of the columns of Z, and
+// the ordering of split problems.
 //
+// The eigenvalue comes in bisected to full relative accuracy (the interval
+// engine's FINAL mode), so a single twisted factorization suffices.
 // Twisted factorization of L D L^T - lambda I at twist index r:
 //   stationary (top-down)   s_1 = -lambda, D+_i = D_i + s_i,
 //                           L+_i = LD_i / D+_i, s_{i+1} = L+_i l_i s_i - lambda
@@ -12,8 +15,7 @@
 //   twist                   gamma_r = s_r + p_r + lambda, r = argmin |gamma_r|
 //   solve N_r z = gamma_r e_r with z_r = 1:
 //                           z_i = -L+_i z_{i+1} (i < r), z_{i+1} = -U-_i z_i (i >= r)
-// The residual of (L D L^T - lambda I) z is |gamma_r| / ||z|| and the
-// Rayleigh-quotient correction is gamma_r / ||z||^2.
+// The residual of (L D L^T - lambda I) z is |gamma_r| / ||z||.
 #include <cmath>
 
 #include "mrrr_launch.h"
@@ -24,13 +26,14 @@ namespace {
 
 // A: L+ (stride as), B: s then U- (stride bs), z: output (stride zs; may alias A).
 // Returns the Sturm count (negative pivots of the stationary part).
-__device__ int twisted_solve(const RepRow* __restrict__ rep, int m, double lam, double pivmin,
+__device__ int twisted_solve(const double2* __restrict__ dl, const double2* __restrict__ ul, int m, double lam,
+                             double pivmin,
                              double* A, int64_t as, double* B, int64_t bs, double* z, int64_t zs,
                              int& r, double& gamma, double& norm2) {
   int negc = 0;
   double s = -lam;
   for (int i = 0; i < m - 1; ++i) {
-    const RepRow R = rep[i];
+    const RepRow R = rep_row(dl, ul, i);
     double dp = R.D + s;
     if (fabs(dp) < pivmin) dp = -pivmin;
     negc += (dp < 0.0);
@@ -40,18 +43,18 @@ __device__ int twisted_solve(const RepRow* __restrict__ rep, int m, double lam, 
     s = fma(lp, R.l * s, -lam);
   }
   {
-    double dp = rep[m - 1].D + s;
+    double dp = dl[m - 1].x + s;
     if (fabs(dp) < pivmin) dp = -pivmin;
     negc += (dp < 0.0);
     B[(int64_t)(m - 1) * bs] = s;
   }
-  double p = rep[m - 1].D - lam;
+  double p = dl[m - 1].x - lam;
   double g = s + p + lam;
   double best = fabs(g);
   r = m - 1;
   gamma = g;
   for (int i = m - 2; i >= 0; --i) {
-    const RepRow R = rep[i];
+    const RepRow R = rep_row(dl, ul, i);
     double dm = R.LLD + p;
     if (fabs(dm) < pivmin) dm = -pivmin;
     double t = R.D / dm;
@@ -86,7 +89,6 @@ __global__ void k_vectors(Dev v) {
   const int64_t tid = gtid(), nthr = gstride();
   const int64_t nslots = v.ctl->nslots;
   double* B = v.vscr + tid;
-  double* Ascr = v.vscr + v.vscr_rows * nthr + tid;
   unsigned long long iters = 0;
   for (int64_t w = tid; w < nslots; w += nthr) {
     const int st = v.state[w];
@@ -104,58 +106,29 @@ __global__ void k_vectors(Dev v) {
       v.znrm2[w] = 1.0;
       continue;
     }
-    double* A = zc ? zc : Ascr;
-    const int64_t as = zc ? 1 : nthr;
-    const RepRow* rep = v.pool + nd.rep;
-    const int j = v.sj[w];
-    double lo = v.lo[w], hi = v.hi[w];
-    const double gap_eff = fmin(v.gap[w], nd.spdiam);
-    const double lgm = log2((double)m);
-    const double tolres = 4.0 * lgm * kEps * gap_eff;
-    const double tolrq = 2.0 * kEps;
-    double lam = 0.5 * (lo + hi), lam_out = lam, n2 = 1.0, last_delta = 0.0;
-    double prev_delta = INFINITY;
-    bool conv = false;
-    for (int it = 0; it < v.max_rq; ++it) {
-      int r;
-      double gamma;
-      int negc = twisted_solve(rep, m, lam, nd.pivmin, A, as, B, nthr, A, as, r, gamma, n2);
-      ++iters;
-      const double resid = fabs(gamma) / sqrt(n2);
-      const double delta = gamma / n2;
-      lam_out = lam + delta;  // Rayleigh-quotient estimate for the z just computed
-      last_delta = delta;
-      if (negc >= j)
-        hi = fmin(hi, lam);
-      else
-        lo = fmax(lo, lam);
-      // converged: residual small against the gap, RQ correction at the
-      // rounding level, or the correction has stopped shrinking at a level
-      // of a few dozen ulps (rounding noise of the representation)
-      if (resid <= tolres || fabs(delta) <= tolrq * fabs(lam) ||
-          (it >= 2 && fabs(delta) >= 0.5 * prev_delta && fabs(delta) <= 64.0 * kEps * fabs(lam))) {
-        conv = true;
-        break;
-      }
-      if (it + 1 == v.max_rq) break;  // keep the z of this iterate
-      prev_delta = fabs(delta);
-      double nl = lam + delta;
-      if (!(nl > lo && nl < hi)) nl = 0.5 * (lo + hi);
-      lam = nl;
+    if (!zc) {  // eigenvalues only: the bisected value is final
+      v.W[q.wout + pos] = (nd.sigma_abs + 0.5 * (v.lo[w] + v.hi[w])) / q.scale;
+      continue;
     }
-    if (!conv) {
-      // iteration cap: the last iterate is kept; only a correction far above
-      // the rounding level is an error
-      diag(v.ctl, DIAG_RQ);
-      if (!(fabs(last_delta) <= 0x1p-20 * fabs(lam))) set_status(v.ctl, MRRR_ERR_NOCONV);
-    }
+    double* A = zc;
+    const int64_t as = 1;
+    const double2* rdl = v.rep_dl + nd.rep;
+    const double2* rul = v.rep_ul + nd.rep;
+    // the eigenvalue was bisected to full relative accuracy on this
+    // representation: one twisted factorization gives the vector
+    const double lam = 0.5 * (v.lo[w] + v.hi[w]);
+    int r;
+    double gamma, n2;
+    twisted_solve(rdl, rul, m, lam, nd.pivmin, A, as, B, nthr, A, as, r, gamma, n2);
+    ++iters;
+    const double lam_out = lam;
     if (!isfinite(n2)) set_status(v.ctl, MRRR_ERR_NOCONV);
     v.W[q.wout + pos] = (nd.sigma_abs + lam_out) / q.scale;
     v.wval[w] = lam_out;
     v.znrm2[w] = n2;
     if (!zc) continue;
   }
-  if (iters) atomicAdd(&v.ctl->rq_iters, iters);
+  if (iters) atomicAdd(&v.ctl->twisted_solves, iters);
 }
 
 // One CTA per output slot: scale the column to unit norm and clear the rows

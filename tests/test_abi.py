@@ -43,7 +43,7 @@ def test_options_defaults(lib):
     assert lib.mrrr_options_default(ctypes.byref(o)) == 0
     assert o.gap_tol == 1e-3
     assert o.classify_rtol == 2.0 ** -20
-    assert o.max_depth == 64 and o.max_rq_iters > 0 and o.threads_per_block % 32 == 0
+    assert o.max_depth == 64 and o.threads_per_block % 32 == 0
     assert lib.mrrr_options_default(None) == _lib.ERR_ARG
 
 
