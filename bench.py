@@ -34,10 +34,23 @@ METRIC = "FP64 tridiagonal eigenpairs/s + roofline fraction; batched & adjoint v
 UNIT = "eigenpairs/s"
 WORKLOAD = "clustered spectra n~20000: Wilkinson W+ n=20001 + glued W21+ x952 (n=19992, glue 1e-10), all eigenpairs"
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070  # SMs x DFMA/clk/SM x flops/DFMA x GHz (max SM clock)
-# Algorithmic FP64 flops per eigenvalue and matrix row for each stage (model
-# fixed in the design notes): bisection 4 flops per row and Sturm step with
-# B = 32 steps; twisted factorization, solve and normalisation 15 per row.
-STAGE_FLOPS_PER_ROW = {"bisect_root": 4 * 32, "prerefine": 4 * 32, "refine": 4 * 32, "vectors": 15}
+# Fixed algorithmic model per eigenpair and matrix row: bisection 4 flops per
+# Sturm step with B = 32 steps, plus 15 flops for the twisted factorization,
+# solve and normalisation; 8 bytes of Z written.
+BISECT_FLOPS_PER_ROW = 4 * 32
+PATH_FLOPS_PER_ROW = BISECT_FLOPS_PER_ROW + 15
+ENGINE_STAGES = ("bisect_root", "prerefine", "refine", "final_bisect")
+
+
+def _hbm_gbs() -> float:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return 6800.0  # fallback figure for this part
+
+
+HBM_GBS = _hbm_gbs()
 
 
 def workload_matrices():
@@ -106,30 +119,55 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU oracle leg (reference arm and cpu_baseline)
 
-def oracle_sample(mats, per_matrix: int, nthreads: int, offset: int = 0):
-    """Eigenpairs of a sample of indices of each matrix by the oracle
-    (bisection on T for lambda_j, inverse iteration for z_j).  Returns
-    (eigenpairs, seconds)."""
-    import oracle
-    from concurrent.futures import ThreadPoolExecutor
-    oracle.build()
+WINDOW = 64  # consecutive eigenpair indices per oracle sample window
+
+
+def oracle_windows(mats, windows: int, offset: int = 0):
+    """`windows` index windows of WINDOW consecutive eigenpairs per matrix,
+    evenly spread over the spectrum (shifted by `offset` so that repeated
+    samples differ)."""
     jobs = []
     for _, d, e in mats:
         n = len(d)
-        idx = np.linspace(1, n, per_matrix).astype(int)
-        idx = np.clip(idx + offset, 1, n)
-        jobs += [(d, e, int(j)) for j in idx]
+        starts = np.linspace(1, n - WINDOW + 1, windows).astype(int)
+        for s0 in starts:
+            il = int(np.clip(s0 + offset, 1, n - WINDOW + 1))
+            jobs.append((d, e, il, il + WINDOW - 1))
+    return jobs
+
+
+def oracle_sample(jobs, nthreads: int):
+    """The oracle as it stands (bisection on T, inverse iteration with
+    Gram-Schmidt inside clusters) on index windows, one window per host
+    thread at a time.  Returns (eigenpairs, seconds)."""
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+    oracle.build()
 
     def one(job):
-        d, e, j = job
-        lam = oracle.kth_eigenvalue(d, e, j)
-        oracle.cluster_vectors(d, e, [lam])
-        return 1
+        d, e, il, iu = job
+        W, _ = oracle.eigh_tridiagonal(d, e, il, iu, nthreads=1)
+        return len(W)
 
     t0 = time.perf_counter()
     with ThreadPoolExecutor(max_workers=nthreads) as ex:
         done = sum(ex.map(one, jobs))
     return done, time.perf_counter() - t0
+
+
+def calibrated_windows(mats, nthreads: int, seconds: float) -> int:
+    """Windows per matrix for a sample of about `seconds` of oracle work."""
+    probe = max(1, nthreads // len(mats))
+    p, t = oracle_sample(oracle_windows(mats, probe), nthreads)
+    per_window = t / (probe * len(mats)) * nthreads  # thread-seconds per window
+    want = seconds * nthreads / per_window / len(mats)
+    return int(np.clip(round(want), 1, 4096))
+
+
+def sample_text(windows: int, nmats: int, cores: int, secs: float) -> str:
+    return (f"{windows} windows x {WINDOW} consecutive eigenpairs per matrix ({windows * WINDOW * nmats} "
+            f"eigenpairs, spread over each spectrum) of the same two matrices: oracle bisection on T + "
+            f"inverse iteration with Gram-Schmidt inside clusters, {cores} threads, {secs:.1f} s")
 
 
 def run_reference(args, rank: int, world: int):
@@ -138,17 +176,18 @@ def run_reference(args, rank: int, world: int):
     import oracle
     mats = workload_matrices()
     cores = oracle.num_threads(0)
-    per = args.ref_sample
+    # each step a bounded sample: the whole run stays within a few minutes
+    per_step_s = float(np.clip(150.0 / max(args.steps + args.warmup, 1), 2.0, 20.0))
+    windows = calibrated_windows(mats, cores, per_step_s)
     for w in range(args.warmup):
-        oracle_sample(mats, max(per // 4, 2), cores, offset=w)
+        oracle_sample(oracle_windows(mats, max(windows // 4, 1), offset=w), cores)
     total_pairs, total_t = 0, 0.0
     for s in range(args.steps):
-        p, t = oracle_sample(mats, per, cores, offset=s + 1)
+        p, t = oracle_sample(oracle_windows(mats, windows, offset=s + 1), cores)
         total_pairs += p
         total_t += t
     value = total_pairs / total_t
-    sample = (f"{per} eigenpairs per matrix per step (evenly spaced indices), oracle bisection on T + "
-              f"inverse iteration, {cores} threads")
+    sample = sample_text(windows, len(mats), cores, total_t / max(args.steps, 1)) + " per step"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -226,49 +265,61 @@ def run_ours(args, rank: int, world: int):
     total_ms = float(tmax.item())
     value = world * pairs_per_step * args.steps / (total_ms * 1e-3)
 
-    # end to end through the public API with host buffers
+    # end to end through the public API with host buffers: d, e copied in
+    # from pinned memory, W and Z copied back into pinned memory, every step
     hostd = [(torch.tensor(d).pin_memory(), torch.tensor(np.append(e, 0.0)).pin_memory()) for _, d, e in mats]
+    hostout = [(torch.empty(len(d), dtype=torch.float64, pin_memory=True),
+                torch.empty((len(d), len(d)), dtype=torch.float64, pin_memory=True)) for _, d, _ in mats]
     h2d = sum(a.numel() * 8 + b.numel() * 8 for a, b in hostd)
-    d2h = pairs_per_step * 8
+    d2h = sum(w.numel() * 8 + z.numel() * 8 for w, z in hostout)
+
+    def e2e_step(check: bool):
+        for (hd, he), (hw, hz), plan in zip(hostd, hostout, plans):
+            W, Z = api.eigh_tridiagonal(hd.to(dev, non_blocking=True), he.to(dev, non_blocking=True), plan=plan,
+                                        check=check)
+            hw.copy_(W, non_blocking=True)
+            hz.copy_(Z.t(), non_blocking=True)  # Z is column-major: its transpose is contiguous
+        torch.cuda.synchronize(dev)
+
     for _ in range(2):
-        for (hd, he), plan in zip(hostd, plans):
-            W, Z = api.eigh_tridiagonal(hd.to(dev, non_blocking=True), he.to(dev, non_blocking=True), plan=plan)
-            W.cpu()
+        e2e_step(check=True)
     barrier()
     e2e_times = []
     for _ in range(args.steps):
         flush.zero_()
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        for (hd, he), plan in zip(hostd, plans):
-            W, Z = api.eigh_tridiagonal(hd.to(dev, non_blocking=True), he.to(dev, non_blocking=True), plan=plan,
-                                        check=False)
-            W.cpu()
-        torch.cuda.synchronize(dev)
+        e2e_step(check=False)
         e2e_times.append(time.perf_counter() - t0)
     e2e_value = world * pairs_per_step * args.steps / sum(e2e_times)
+    del hostout
 
-    # roofline of the dominant stage
-    dom = max(stage_ms, key=stage_ms.get) if stage_ms else None
+    # roofline of the dominant kernel: the persistent interval engine (every
+    # bisection stage), against the bisection part of the fixed flop model
+    engine_ms = sum(stage_ms.get(k, 0.0) for k in ENGINE_STAGES) / args.steps
+    nk = sum(len(d) * len(d) for _, d, _ in mats)  # rows x eigenpairs per step
     roof = None
-    if dom:
-        per_launch_ms = stage_ms[dom] / args.steps / len(mats)
-        rows = sum(len(d) * len(d) for _, d, _ in mats) / len(mats)  # eigenvalues x rows per solve
-        flops = STAGE_FLOPS_PER_ROW.get(dom, 4 * 32) * rows
-        achieved = flops / (per_launch_ms * 1e-3) / 1e9
-        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None,
-                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz"}
+    if engine_ms > 0:
+        achieved = BISECT_FLOPS_PER_ROW * nk / (engine_ms * 1e-3) / 1e9
+        roof = {"bound": "alu", "kernel": "k_engine (interval bisection, all modes)", "achieved": achieved,
+                "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS,
+                "traffic": None, "engine_ms_per_step": engine_ms,
+                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz (max SM clock)"}
+    # whole path against T_roof = max(F / P_fp64, 8 n k / BW), F = 143 n k
+    t_flop = PATH_FLOPS_PER_ROW * nk / (FP64_PEAK_GFLOPS * 1e9)
+    t_hbm = 8.0 * nk / (HBM_GBS * 1e9)
+    t_roof_ms = 1e3 * max(t_flop, t_hbm)
+    path_roof = {"t_roof_ms": t_roof_ms, "t_step_ms": total_ms / args.steps,
+                 "frac": t_roof_ms / (total_ms / args.steps), "bound": "alu" if t_flop >= t_hbm else "hbm",
+                 "model": "143 n flops + 8 n bytes per eigenpair", "hbm_gbs": HBM_GBS}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         cores = oracle.num_threads(0)
-        per = args.ref_sample
-        oracle_sample(mats, 4, cores)
-        p, t = oracle_sample(mats, per, cores, offset=1)
+        windows = calibrated_windows(mats, cores, args.cpu_seconds)
+        p, t = oracle_sample(oracle_windows(mats, windows, offset=1), cores)
         cpu = {"value": p / t, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"{per} eigenpairs per matrix (evenly spaced indices) of the same two matrices: "
-                         f"oracle bisection on T + inverse iteration, {t:.1f} s"}
+               "sample": sample_text(windows, len(mats), cores, t)}
     clocks = clk.summary()
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -279,7 +330,7 @@ def run_ours(args, rank: int, world: int):
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "clocks": clocks, "gpu_launches": launches,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "roofline": roof, "cpu_baseline": cpu,
+            "roofline": roof, "path_roofline": path_roof, "cpu_baseline": cpu,
             "stages_ms_per_step": {k: v / args.steps for k, v in sorted(stage_ms.items())}}
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -291,7 +342,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--ref-sample", type=int, default=48, help="oracle eigenpairs per matrix per step")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target length of the cpu_baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))

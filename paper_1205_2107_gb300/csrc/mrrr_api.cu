@@ -50,9 +50,12 @@ void StageTimer::finish() {
     return;
   }
   cudaEventSynchronize(ev[count - 1]);
+  const char* env = std::getenv("MRRR_TIMING");
+  const bool each = env && std::strcmp(env, "2") == 0;  // every stage in launch order
   for (int i = 1; i < count; ++i) {
     float t = 0.f;
     cudaEventElapsedTime(&t, ev[i - 1], ev[i]);
+    if (each) std::fprintf(stderr, "[mrrr stage %3d] %-18s %10.3f ms\n", i, name[i], t);
     int k = 0;
     while (k < nstages && std::strcmp(stage_name[k], name[i]) != 0) ++k;
     if (k == nstages) {
