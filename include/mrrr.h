@@ -173,6 +173,40 @@ mrrr_status mrrr_backward(mrrr_plan* plan, int batch, const int64_t* d_off, cons
 /* Bytes of workspace mrrr_backward needs for batch problems of order <= n_max. */
 mrrr_status mrrr_backward_workspace_size(const mrrr_plan* plan, int batch, int n_max, size_t* bytes);
 
+/*
+ * mrrr_eigenvalues_static: eigenvalues il..iu of one symmetric tridiagonal T
+ * without allocating anything and without a caller workspace.  The paper has
+ * no counterpart: this exists for callers that cannot call cudaMalloc when
+ * they need eigenvalues -- a process whose device memory is already reserved
+ * by another allocator (a framework's caching allocator), or a
+ * latency-sensitive loop that cannot afford cudaFree's device-wide
+ * synchronisation.
+ *   n          order of T, 0 <= n <= MRRR_STATIC_MAX_N (n = 0 is a no-op);
+ *              larger n returns MRRR_ERR_ARG before any GPU work
+ *   d, e       device, d[n] diagonal, e[n-1] off-diagonal (read only)
+ *   il, iu     1-based inclusive range, 1 <= il <= iu <= n
+ *   W          device, W[iu-il+1] eigenvalues, ascending, each bisected to
+ *              full accuracy on the root representation T - sigma I = L D L^T
+ *   stream     CUDA stream of the two launches; the call returns before the
+ *              GPU has finished
+ * Scratch is one array of (32 + 2 * MRRR_STATIC_MAX_N) doubles (about
+ * 128 KiB) in the library's static device memory, which each GPU that loads
+ * the library holds until the process exits.  Every call on a device uses
+ * the same array and leaves its contents behind; each call rewrites all it
+ * later reads (header and status word first), so no state carries over.
+ * Calls whose work overlaps on the GPU (different streams, or different host
+ * threads, on the same device) race on the array and give wrong results:
+ * serialise them.  The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress, with that device current) and caches it;
+ * make that first call before any stream capture.  Device-side errors
+ * (non-finite input, no definite root shift) give NaN eigenvalues.  Returns
+ * MRRR_ERR_ARG for bad host-side arguments and MRRR_ERR_CUDA when the
+ * address lookup or a launch fails.
+ */
+#define MRRR_STATIC_MAX_N 8192
+mrrr_status mrrr_eigenvalues_static(int n, const double* d, const double* e, int il, int iu, double* W,
+                                    mrrr_stream stream);
+
 /* Stage profile of the last solve on a plan.  launches counts the kernels
    the solve enqueued; when timing is enabled (mrrr_set_timing) the solve
    records CUDA events between its stages on its stream and ms[i] holds the

@@ -22,7 +22,9 @@ OK, ERR_ARG, ERR_WORKSPACE, ERR_NONFINITE, ERR_NOCONV, ERR_QUEUE, ERR_TIMEOUT, E
 # every function include/mrrr.h declares
 EXPORTS = ["mrrr_options_default", "mrrr_plan_create", "mrrr_plan_destroy", "mrrr_workspace_size",
            "mrrr_stein", "mrrr_stein_batched", "mrrr_backward", "mrrr_backward_workspace_size",
-           "mrrr_get_status", "mrrr_status_string", "mrrr_version", "mrrr_set_timing", "mrrr_get_profile"]
+           "mrrr_get_status", "mrrr_status_string", "mrrr_version", "mrrr_set_timing", "mrrr_get_profile",
+           "mrrr_eigenvalues_static"]
+STATIC_MAX_N = 8192  # MRRR_STATIC_MAX_N
 
 
 class Options(ctypes.Structure):
@@ -93,6 +95,7 @@ def load(build_if_missing: bool = False):
         lib.mrrr_version.argtypes = []
         lib.mrrr_set_timing.argtypes = [P, c_int]
         lib.mrrr_get_profile.argtypes = [P, ctypes.POINTER(Profile)]
+        lib.mrrr_eigenvalues_static.argtypes = [c_int, dp, dp, c_int, c_int, dp, P]
         for name in EXPORTS:
             if name not in ("mrrr_status_string", "mrrr_version"):
                 getattr(lib, name).restype = c_int
