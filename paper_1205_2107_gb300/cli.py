@@ -1,0 +1,65 @@
+"""Command-line solve of one synthetic tridiagonal (for timing and profiling).
+
+    python -m paper_1205_2107_gb300.cli --family wilkinson --n 4001 --repeat 3
+
+Families are the seeded generators of ``inputs``: uniform (d, e iid
+U[-1, 1]), normal, toeplitz (d = 2, e = -1), wilkinson (W+), glued (copies of
+W21+ glued by 1e-10; --n is the number of copies), clement, large (d U[0,1],
+e U[0, 1e-2]).  Prints the stage profile of the last solve as one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+import numpy as np
+import torch
+
+from . import api, inputs
+
+FAMILIES = {
+    "uniform": lambda n, seed: inputs.uniform(n, seed),
+    "normal": lambda n, seed: inputs.normal(n, seed),
+    "toeplitz": lambda n, seed: inputs.toeplitz(n),
+    "wilkinson": lambda n, seed: inputs.wilkinson_plus(n),
+    "glued": lambda n, seed: inputs.glued_wilkinson(n),
+    "clement": lambda n, seed: inputs.clement(n),
+    "large": lambda n, seed: inputs.large_uniform(n, seed),
+}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--family", choices=sorted(FAMILIES), default="uniform")
+    ap.add_argument("--n", type=int, default=1000)
+    ap.add_argument("--seed", type=int, default=1205)
+    ap.add_argument("--il", type=int, default=None)
+    ap.add_argument("--iu", type=int, default=None)
+    ap.add_argument("--repeat", type=int, default=1)
+    ap.add_argument("--values-only", action="store_true")
+    args = ap.parse_args(argv)
+    d, e = FAMILIES[args.family](args.n, args.seed)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    dd = torch.tensor(d, device=dev)
+    ee = torch.tensor(np.append(e, 0.0), device=dev)
+    plan = api.Plan(dev)
+    plan.set_timing(True)
+    times = []
+    for _ in range(args.repeat):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        api.eigh_tridiagonal(dd, ee, args.il, args.iu, plan=plan, vectors=not args.values_only, check=False)
+        ev1.record()
+        ev1.synchronize()
+        times.append(ev0.elapsed_time(ev1))
+    info = plan.info()
+    prof = plan.profile()
+    print(json.dumps({"family": args.family, "n": len(d), "ms": times, "status": info["status"],
+                      "depth": info["depth"], "nodes": info["nodes"], "launches": prof["launches"],
+                      "stages_ms": prof["stages"]}))
+    if info["status"] != 0:
+        raise SystemExit(f"solver status {info['status']}")
+
+
+if __name__ == "__main__":
+    main()
