@@ -105,19 +105,21 @@ __global__ void k_classify_runs(Dev v, int level) {
 // growth_only: returns max |D+_i| without storing (infinite when a pivot is
 // not finite); otherwise writes the child rows and returns
 // max(|D+_i|, |LLD+_i|).
+// growth_d receives max |D+_i| (infinite when a pivot is not finite) in both
+// forms.
 template <bool kStore>
 __device__ double dstqds_child(const double2* __restrict__ pdl, const double2* __restrict__ pul,
                                double2* __restrict__ cdl, double2* __restrict__ cul, int m, double sigma,
-                               double pivmin) {
+                               double pivmin, double* growth_d = nullptr) {
   double s = -sigma;
-  double growth = 0.0;
+  double gd = 0.0, growth = 0.0;
   for (int i = 0; i < m - 1; ++i) {
     const RepRow r = rep_row(pdl, pul, i);
     double dp = r.D + s;
     if (fabs(dp) < pivmin) dp = -pivmin;
     const double lp = r.LD / dp;
     s = fma(lp, r.l * s, -sigma);
-    growth = fmax(growth, fabs(dp));
+    gd = fmax(gd, fabs(dp));
     if (kStore) {
       const double ldp = lp * dp;
       const double lldp = lp * ldp;
@@ -128,64 +130,106 @@ __device__ double dstqds_child(const double2* __restrict__ pdl, const double2* _
   double dp = pdl[m - 1].x + s;
   if (fabs(dp) < pivmin) dp = -pivmin;
   if (kStore) rep_store(cdl, cul, m - 1, RepRow{dp, 0.0, 0.0, 0.0});
-  growth = fmax(growth, fabs(dp));
+  gd = fmax(gd, fabs(dp));
+  if (!isfinite(gd)) gd = INFINITY;
+  growth = fmax(growth, gd);
   if (!isfinite(growth)) growth = INFINITY;
-  return growth;
+  if (growth_d) *growth_d = gd;
+  return kStore ? growth : gd;
 }
 
 constexpr int kShiftTries = 10;  // per side
 
-// One warp per new node: the lanes evaluate 2 x kShiftTries candidate
-// shifts at once -- the left end lo_f - delta_t and the right end
-// hi_l + delta_t of the cluster, delta_t = 4 eps |end| 4^t -- and the first
-// candidate (in the order t = 0, 1, ..., left before right) whose element
-// growth max|D+| is at most 8 spdiam is taken; if none is, the candidate with
-// the smallest growth (counted in the diagnostics).  The chosen transform is
-// then recomputed with stores into rows of the representation pool.
-__global__ void k_childrep(Dev v) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = gtid() >> 5, nwarps = gstride() >> 5;
+// Candidate shift t (0 .. 2 kShiftTries - 1) of a cluster: even t the left
+// end lo_f - delta, odd t the right end hi_l + delta, delta = 4 eps |end| 4^(t/2)
+// (+ 4 pivmin).
+__device__ __forceinline__ double child_shift(int t, double lo_f, double hi_l, double pivmin) {
+  const int side = t & 1, k = t >> 1;
+  const double ref = side == 0 ? lo_f : hi_l;
+  const double delta = 4.0 * kEps * fabs(ref) * (double)(1LL << (2 * k)) + 4.0 * pivmin;
+  return side == 0 ? lo_f - delta : hi_l + delta;
+}
+
+__device__ __forceinline__ void set_child(Dev& v, int64_t id, Node c, const Node& p, int64_t base, double sigma,
+                                          double R) {
+  c.rep = base;
+  c.sigma_rel = sigma;
+  c.sigma_abs = p.sigma_abs + sigma;
+  c.pivmin = pivmin_for(R);
+  c.pad_ = 0;
+  v.node[id] = c;
+}
+
+// Child representations, phase 1: one thread per new node reserves its rows
+// in the representation pool and builds the transform for the first
+// candidate shift (the left end of the cluster, smallest offset) with the
+// stores done in the same pass.  It is kept when its element growth max|D+|
+// is at most 8 spdiam; otherwise the node is marked for phase 2.  Nodes
+// whose rows do not fit take the fallback (their vectors at the parent).
+__global__ void k_childrep_first(Dev v) {
   const int begin = v.ctl->level_begin;
   const int end = min(v.ctl->nodes, v.max_nodes);
-  for (int64_t id = begin + warp; id < end; id += nwarps) {
+  for (int64_t id = begin + gtid(); id < end; id += gstride()) {
     Node c = v.node[id];
     const Node p = v.node[c.parent];
     const int m = v.blk[c.block].m;
-    int64_t base = 0;
-    if (lane == 0) {
-      base = (int64_t)atomicAdd((unsigned long long*)&v.ctl->pool_top, (unsigned long long)m);
-      atomicMax((unsigned long long*)&v.ctl->pool_need, (unsigned long long)(base + m));
-    }
-    base = __shfl_sync(0xffffffffu, base, 0);
+    const int64_t base =
+        (int64_t)atomicAdd((unsigned long long*)&v.ctl->pool_top, (unsigned long long)m);
+    atomicMax((unsigned long long*)&v.ctl->pool_need, (unsigned long long)(base + m));
     if (base + m > v.pool_cap) {
       set_status(v.ctl, MRRR_ERR_QUEUE);
       // vectors of these slots are taken at the parent node
-      for (int64_t t = c.first + lane; t <= c.last; t += 32) {
+      for (int64_t t = c.first; t <= c.last; ++t) {
         v.state[t] = SLOT_FALLBACK;
         v.snode[t] = c.parent;
         double a = (t == c.first) ? c.gapl : v.lo[t] - v.hi[t - 1];
         double b = (t == c.last) ? c.gapr : v.lo[t + 1] - v.hi[t];
         v.gap[t] = fmax(fmin(a, b), 0.0);
       }
-      if (lane == 0) {
-        atomicAdd(&v.ctl->fallbacks, (unsigned long long)(c.last - c.first + 1));
-        diag(v.ctl, DIAG_CAPACITY, (unsigned long long)(c.last - c.first + 1));
-        c.rep = -1;
-        c.depth = -1;  // inert
-        v.node[id] = c;
-      }
+      atomicAdd(&v.ctl->fallbacks, (unsigned long long)(c.last - c.first + 1));
+      diag(v.ctl, DIAG_CAPACITY, (unsigned long long)(c.last - c.first + 1));
+      c.rep = -1;
+      c.depth = -1;  // inert
+      v.node[id] = c;
       continue;
     }
+    const double sigma = child_shift(0, v.lo[c.first], v.hi[c.last], p.pivmin);
+    double gd;
+    const double R = dstqds_child<true>(v.rep_dl + p.rep, v.rep_ul + p.rep, v.rep_dl + base, v.rep_ul + base, m,
+                                        sigma, p.pivmin, &gd);
+    if (gd <= 8.0 * c.spdiam) {
+      set_child(v, id, c, p, base, sigma, R);
+    } else {
+      c.rep = base;
+      c.pad_ = 1;  // phase 2
+      v.node[id] = c;
+    }
+  }
+}
+
+// Phase 2, one warp per node whose first candidate failed: the lanes
+// evaluate all 2 x kShiftTries candidate shifts at once (growth only), the
+// first candidate in the order of child_shift whose growth max|D+| is at most
+// 8 spdiam is taken, else the one with the smallest growth (counted in the
+// diagnostics); the chosen transform is then recomputed with stores into the
+// rows reserved in phase 1.
+__global__ void k_childrep(Dev v) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = gtid() >> 5, nwarps = gstride() >> 5;
+  const int begin = v.ctl->level_begin;
+  const int end = min(v.ctl->nodes, v.max_nodes);
+  for (int64_t id = begin + warp; id < end; id += nwarps) {
+    const Node c = v.node[id];
+    if (c.pad_ != 1) continue;
+    const Node p = v.node[c.parent];
+    const int m = v.blk[c.block].m;
     const double2* pdl = v.rep_dl + p.rep;
     const double2* pul = v.rep_ul + p.rep;
     const double lo_f = v.lo[c.first], hi_l = v.hi[c.last];
     const double bound = 8.0 * c.spdiam;
     double sigma = lo_f, g = INFINITY;
     if (lane < 2 * kShiftTries) {
-      const int side = lane & 1, t = lane >> 1;
-      const double ref = side == 0 ? lo_f : hi_l;
-      const double delta = 4.0 * kEps * fabs(ref) * (double)(1LL << (2 * t)) + 4.0 * p.pivmin;
-      sigma = side == 0 ? lo_f - delta : hi_l + delta;
+      sigma = child_shift(lane, lo_f, hi_l, p.pivmin);
       g = dstqds_child<false>(pdl, pul, nullptr, nullptr, m, sigma, p.pivmin);
     }
     const unsigned okmask = __ballot_sync(0xffffffffu, g <= bound);
@@ -205,12 +249,8 @@ __global__ void k_childrep(Dev v) {
     }
     sigma = __shfl_sync(0xffffffffu, sigma, pick);
     if (lane == 0) {
-      const double R = dstqds_child<true>(pdl, pul, v.rep_dl + base, v.rep_ul + base, m, sigma, p.pivmin);
-      c.rep = base;
-      c.sigma_rel = sigma;
-      c.sigma_abs = p.sigma_abs + sigma;
-      c.pivmin = pivmin_for(R);
-      v.node[id] = c;
+      const double R = dstqds_child<true>(pdl, pul, v.rep_dl + c.rep, v.rep_ul + c.rep, m, sigma, p.pivmin);
+      set_child(v, id, c, p, c.rep, sigma, R);
     }
   }
 }
@@ -230,6 +270,8 @@ void launch_level_children(const Dev& v, int level, const Grid& g, cudaStream_t 
   (void)level;
   launch_engine(v, 1, g, s);
   mark_stage("prerefine", s);
+  k_childrep_first<<<g.slot_blocks, 128, 0, s>>>(v);
+  count_launch();
   k_childrep<<<g.slot_blocks, 128, 0, s>>>(v);
   count_launch();
   mark_stage("childrep", s);
