@@ -7,10 +7,13 @@ load lazily so that ``paper_1205_2107_gb300.inputs`` imports without torch.
 import importlib
 
 __all__ = ["Plan", "BatchLayout", "eigh_tridiagonal", "eigh_tridiagonal_batched", "build", "inputs",
-           "EighTridiagonal", "eigh_tridiagonal_autograd"]
+           "EighTridiagonal", "eigh_tridiagonal_autograd", "EighTridiagonalBatched",
+           "eigh_tridiagonal_batched_autograd", "eigh_tridiagonal_backward"]
 
 _LAZY = {"Plan": "api", "BatchLayout": "api", "eigh_tridiagonal": "api", "eigh_tridiagonal_batched": "api",
-         "default_plan": "api", "EighTridiagonal": "autograd", "eigh_tridiagonal_autograd": "autograd"}
+         "default_plan": "api", "eigh_tridiagonal_backward": "api", "EighTridiagonal": "autograd",
+         "eigh_tridiagonal_autograd": "autograd", "EighTridiagonalBatched": "autograd",
+         "eigh_tridiagonal_batched_autograd": "autograd"}
 
 
 def __getattr__(name):

@@ -87,8 +87,8 @@ def load(build_if_missing: bool = False):
         lib.mrrr_stein.argtypes = [P, c_int, dp, dp, c_int, c_int, dp, dp, c_int64, dp, c_size_t, P]
         lib.mrrr_stein_batched.argtypes = [P, c_int, dp, dp, dp, dp, dp, dp, dp, dp, dp, c_int64, c_int64,
                                            c_int, dp, c_size_t, P]
-        lib.mrrr_backward.argtypes = [P, c_int, dp, dp, dp, dp, dp, c_double, c_int, dp, dp, dp, c_size_t, P]
-        lib.mrrr_backward_workspace_size.argtypes = [P, c_int, c_int, ctypes.POINTER(c_size_t)]
+        lib.mrrr_backward.argtypes = [P, c_int, dp, dp, dp, dp, dp, c_double, c_int, c_int64, dp, dp, dp, c_size_t, P]
+        lib.mrrr_backward_workspace_size.argtypes = [P, c_int, c_int64, ctypes.POINTER(c_size_t)]
         lib.mrrr_get_status.argtypes = [P, P, ctypes.POINTER(Info)]
         lib.mrrr_status_string.argtypes = [c_int]
         lib.mrrr_status_string.restype = ctypes.c_char_p

@@ -267,3 +267,40 @@ def eigh_tridiagonal_batched(d: torch.Tensor, e: torch.Tensor, layout: BatchLayo
                         Z, layout.z_offsets if vectors else None, layout.n_total, layout.k_total, layout.n_max)
     _run_with_retry(plan, call, "mrrr_stein_batched", check)
     return (W, Z) if vectors else W
+
+
+def eigh_tridiagonal_backward(W: torch.Tensor, Z: torch.Tensor, Wbar: torch.Tensor | None,
+                              Zbar: torch.Tensor | None, layout: BatchLayout, *, tau_rel: float = 0.0,
+                              plan: Plan | None = None, check: bool = True):
+    """Gradient (dbar, ebar) of a loss with respect to packed (d, e), given
+    the packed all-eigenpair solution (W, Z) of ``layout`` and the loss
+    gradients Wbar (like W) and Zbar (like Z); either may be None.
+
+    dbar and ebar have the packing of d and e (ebar's last entry of each
+    problem is 0).  F(i, j) = 1/(W_j - W_i) is dropped where the gap is at
+    most tau_rel * max|W| of the problem.
+    """
+    if not layout.all:
+        raise ValueError("the backward pass needs all eigenpairs of every problem")
+    W = _check_input(W, "W")
+    Z = _check_input(Z, "Z")
+    Wbar = _check_input(Wbar, "Wbar") if Wbar is not None else None
+    Zbar = _check_input(Zbar, "Zbar") if Zbar is not None else None
+    dev = W.device
+    plan = plan or default_plan(dev)
+    n_total = layout.n_total
+    dbar = torch.empty(max(n_total, 1), dtype=_F64, device=dev)
+    ebar = torch.empty(max(n_total, 1), dtype=_F64, device=dev)
+    lib = _lib.load()
+    nbytes = ctypes.c_size_t(0)
+    _lib.check(lib.mrrr_backward_workspace_size(plan.handle, layout.batch, layout.z_total, ctypes.byref(nbytes)),
+               "mrrr_backward_workspace_size")
+    # own buffer: the solve's workspace keeps its status word for info()
+    ws = torch.empty(max(nbytes.value, 256), dtype=torch.uint8, device=dev)
+    rc = lib.mrrr_backward(plan.handle, layout.batch, _ptr(layout.offsets), _ptr(W), _ptr(Z), _ptr(Wbar),
+                           _ptr(Zbar), float(tau_rel), layout.n_max, layout.z_total, _ptr(dbar), _ptr(ebar),
+                           _ptr(ws), nbytes.value, _stream_handle(dev))
+    _lib.check(rc, "mrrr_backward")
+    if check:
+        torch.cuda.synchronize(dev)
+    return dbar[:n_total], ebar[:n_total]

@@ -1,0 +1,85 @@
+"""torch.autograd wrappers: eigenpairs of symmetric tridiagonals with a
+backward pass through the library's adjoint kernels (mrrr_backward).
+
+    W, Z = eigh_tridiagonal_autograd(d, e)          # d (n,), e (n-1,) or (n,)
+    loss = (w * W).sum() + ((C * Z).sum(0) ** 2).sum()
+    loss.backward()                                 # d.grad, e.grad
+
+The gradient follows first-order perturbation theory of T = Z diag(W) Z^T
+(dbar_j = Tbar(j,j), ebar_j = Tbar(j,j+1) + Tbar(j+1,j) for
+Tbar = Z (diag(Wbar) + F o (Z^T Zbar)) Z^T); it is defined for losses that
+do not depend on the signs of the columns of Z, and for separated
+eigenvalues (gaps at most tau_rel * max|W| are dropped from F).
+"""
+from __future__ import annotations
+
+import torch
+
+from . import api
+
+
+class EighTridiagonal(torch.autograd.Function):
+    """One problem: (d, e) -> (W, Z), all eigenpairs."""
+
+    @staticmethod
+    def forward(ctx, d, e, tau_rel=0.0, plan=None):
+        W, Z = api.eigh_tridiagonal(d.detach(), e.detach(), plan=plan)
+        ctx.tau_rel = float(tau_rel)
+        ctx.plan = plan
+        ctx.e_numel = e.numel()
+        ctx.save_for_backward(W, Z)
+        return W, Z
+
+    @staticmethod
+    def backward(ctx, gW, gZ):
+        W, Z = ctx.saved_tensors
+        n = W.numel()
+        layout = api.BatchLayout([n], W.device)
+        Zflat = Z.t().contiguous().view(-1)  # column-major storage of Z
+        Zb = gZ.t().contiguous().view(-1) if gZ is not None else None
+        Wb = gW.contiguous() if gW is not None else None
+        dbar, ebar = api.eigh_tridiagonal_backward(W, Zflat, Wb, Zb, layout, tau_rel=ctx.tau_rel, plan=ctx.plan)
+        ge = torch.zeros(ctx.e_numel, dtype=dbar.dtype, device=dbar.device)
+        m = min(ctx.e_numel, max(n - 1, 0))
+        ge[:m] = ebar[:m]
+        return dbar, ge, None, None
+
+
+class EighTridiagonalBatched(torch.autograd.Function):
+    """A batch packed by an all-eigenpair BatchLayout: (d, e) -> packed (W, Z)."""
+
+    @staticmethod
+    def forward(ctx, d, e, layout, tau_rel=0.0, plan=None):
+        if not layout.all:
+            raise ValueError("autograd needs all eigenpairs of every problem")
+        W, Z = api.eigh_tridiagonal_batched(d.detach(), e.detach(), layout, plan=plan)
+        W = W[:layout.k_total]
+        Z = Z[:layout.z_total]
+        ctx.layout = layout
+        ctx.tau_rel = float(tau_rel)
+        ctx.plan = plan
+        ctx.e_numel = e.numel()
+        ctx.save_for_backward(W, Z)
+        return W, Z
+
+    @staticmethod
+    def backward(ctx, gW, gZ):
+        W, Z = ctx.saved_tensors
+        Wb = gW.contiguous() if gW is not None else None
+        Zb = gZ.contiguous() if gZ is not None else None
+        dbar, ebar = api.eigh_tridiagonal_backward(W, Z, Wb, Zb, ctx.layout, tau_rel=ctx.tau_rel, plan=ctx.plan)
+        ge = torch.zeros(ctx.e_numel, dtype=dbar.dtype, device=dbar.device)
+        m = min(ctx.e_numel, ebar.numel())
+        ge[:m] = ebar[:m]
+        return dbar, ge, None, None, None
+
+
+def eigh_tridiagonal_autograd(d: torch.Tensor, e: torch.Tensor, *, tau_rel: float = 0.0, plan=None):
+    """All eigenpairs (W, Z) of one tridiagonal, differentiable in (d, e)."""
+    return EighTridiagonal.apply(d, e, tau_rel, plan)
+
+
+def eigh_tridiagonal_batched_autograd(d: torch.Tensor, e: torch.Tensor, layout, *, tau_rel: float = 0.0,
+                                      plan=None):
+    """Packed all-eigenpair solution of a batch, differentiable in (d, e)."""
+    return EighTridiagonalBatched.apply(d, e, layout, tau_rel, plan)
