@@ -57,7 +57,8 @@ typedef enum mrrr_status {
 /* Tunables.  Zero-initialise and call mrrr_options_default(); fields left at
    0 keep their defaults. */
 typedef struct mrrr_options {
-  double gap_tol;          /* singleton threshold on the relative gap (1e-3, Sec. 3.1.1) */
+  double gap_tol;          /* singleton threshold on the relative gap (1e-3, Sec. 3.1.1);
+                              a block of order m < 1000 uses max(gap_tol, 1/m) */
   double classify_rtol;    /* relative interval width reached by bisection before
                               classification (2^-20) */
   int max_depth;           /* cluster-tree depth limit (64); deeper clusters take the
@@ -91,7 +92,9 @@ typedef struct mrrr_info {
                               [1] root bisection cap, [2] child bracket not
                               confirmed, [3] child bisection cap, [4] unused,
                               [5] child growth bound missed, [6] depth-limit
-                              fallbacks, [7] capacity fallbacks, [8]-[11] unused */
+                              fallbacks, [7] capacity fallbacks, [8] runs of
+                              neighbouring eigenvectors re-orthogonalised,
+                              [9]-[11] unused */
 } mrrr_info;
 
 typedef struct mrrr_plan mrrr_plan;
@@ -156,22 +159,34 @@ mrrr_status mrrr_stein_batched(mrrr_plan* plan, int batch, const int64_t* d_off,
  * for a batch of problems solved for ALL eigenpairs, given Wbar = dL/dW and
  * Zbar = dL/dZ (either may be NULL).  Not in the paper: first-order
  * perturbation theory of T = Z diag(W) Z^T,
- *   dbar_j = sum_i Wbar_i Z(j,i)^2 + M(j,j),
- *   ebar_j = 2 sum_i Wbar_i Z(j,i) Z(j+1,i) + M(j,j+1) + M(j+1,j),
- *   M = Z (F o (Z^T Zbar)) Z^T,  F(i,j) = 1/(W_j - W_i) if |W_j - W_i| > tau,
- *   tau = tau_rel * max|W| of the problem; F(i,j) = 0 otherwise.
- *   d_off      device int64[batch+1] as in mrrr_stein_batched (Z is n_p x n_p
- *              at z offset sum_{q<p} n_q^2, W at d_off[p])
+ *   Tbar = Z (diag(Wbar) + F o (Z^T Zbar)) Z^T,
+ *   F(i,j) = 1/(W_j - W_i) if |W_j - W_i| > tau, else 0 (0 on the diagonal),
+ *   tau = tau_rel * max|W| of the problem,
+ *   dbar_j = Tbar(j,j),  ebar_j = Tbar(j,j+1) + Tbar(j+1,j),
+ * so dbar_j = sum_i Wbar_i Z(j,i)^2 + ..., ebar_j = 2 sum_i Wbar_i Z(j,i)
+ * Z(j+1,i) + ....  The two n^3 contractions run on the FP64 tensor cores.
+ *   d_off      device int64[batch+1] as in mrrr_stein_batched; W and Wbar
+ *              use the same packing (n_p values of problem p at d_off[p])
+ *   Z, Zbar    device; problem p's n_p x n_p column-major block starts at
+ *              sum_{q<p} n_q^2 (the packing of mrrr_stein_batched for all
+ *              eigenpairs); z_total = sum_p n_p^2
+ *   tau_rel    >= 0, gap threshold of F relative to max|W|
+ *   n_max      largest n_p (grid sizing)
  *   dbar, ebar device outputs with the packing of d and e (ebar's last entry
  *              of each problem is written as 0)
+ *   workspace  device, ws_bytes >= mrrr_backward_workspace_size(...)
+ * Deterministic (fixed reduction order).  Returns MRRR_ERR_ARG /
+ * MRRR_ERR_WORKSPACE for bad host-side arguments, MRRR_ERR_CUDA when a launch
+ * fails.
  */
 mrrr_status mrrr_backward(mrrr_plan* plan, int batch, const int64_t* d_off, const double* W,
                           const double* Z, const double* Wbar, const double* Zbar, double tau_rel,
-                          int n_max, double* dbar, double* ebar, void* workspace, size_t ws_bytes,
-                          mrrr_stream stream);
+                          int n_max, int64_t z_total, double* dbar, double* ebar, void* workspace,
+                          size_t ws_bytes, mrrr_stream stream);
 
-/* Bytes of workspace mrrr_backward needs for batch problems of order <= n_max. */
-mrrr_status mrrr_backward_workspace_size(const mrrr_plan* plan, int batch, int n_max, size_t* bytes);
+/* Bytes of workspace mrrr_backward needs for batch problems with
+   z_total = sum_p n_p^2. */
+mrrr_status mrrr_backward_workspace_size(const mrrr_plan* plan, int batch, int64_t z_total, size_t* bytes);
 
 /*
  * mrrr_eigenvalues_static: eigenvalues il..iu of one symmetric tridiagonal T

@@ -119,7 +119,7 @@ enum : int {
   DIAG_CHILD_GROWTH = 5,   // no child shift met the growth bound (clusters)
   DIAG_DEPTH = 6,          // depth-limit fallback (eigenvalues)
   DIAG_CAPACITY = 7,       // node table / pool full fallback (eigenvalues)
-  DIAG_SPARE8 = 8,
+  DIAG_ORTH_FIX = 8,       // runs of neighbouring vectors re-orthogonalised
   DIAG_SPARE9 = 9,
   DIAG_SPARE10 = 10,
   DIAG_SPARE11 = 11,

@@ -22,6 +22,13 @@ __global__ void k_level_start(Dev v) {
 
 // Boundary flags: a cluster ends after slot w when the (lower bound of the)
 // absolute gap to w+1 is at least tol times the larger magnitude of the two.
+// tol = max(gap_tol, 1 / m) for a block of order m: the vector of a
+// singleton has an error angle of about c eps / relgap with c of order one
+// and no factor m (Eq. errorangle with a residual of a few ulps of the local
+// eigenvalue), while the orthogonality goal scales with m; below m = 1000 the
+// larger threshold keeps c eps / relgap well under m eps.
+constexpr double kSmallBlockTol = 1.0;
+
 __global__ void k_classify_flags(Dev v, int level) {
   const int64_t nslots = v.ctl->nslots;
   for (int64_t w = gtid(); w < nslots; w += gstride()) {
@@ -33,7 +40,8 @@ __global__ void k_classify_flags(Dev v, int level) {
       double lo0 = v.lo[w], hi0 = v.hi[w], lo1 = v.lo[w + 1], hi1 = v.hi[w + 1];
       double gap = lo1 - hi0;
       double mag = fmax(fmax(fabs(lo0), fabs(hi0)), fmax(fabs(lo1), fabs(hi1)));
-      f = gap >= v.gap_tol * mag;
+      const double tol = fmax(v.gap_tol, kSmallBlockTol / (double)v.blk[nd.block].m);
+      f = gap >= tol * mag;
     }
     v.bflag[w] = f;
   }

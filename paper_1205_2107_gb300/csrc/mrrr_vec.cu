@@ -155,6 +155,102 @@ __global__ void k_normalize(Dev v) {
   }
 }
 
+// Orthogonality safeguard.  A singleton computed on a representation with
+// large element growth can carry an error of c eps / relgap along its
+// nearest neighbours with c well above one; the inner products with the next
+// kOrthNeighbors columns of the same block find such pairs, and runs of
+// linked columns are re-orthogonalised (modified Gram-Schmidt, twice, in
+// eigenvalue order), which removes exactly that component: the residual of a
+// changed column grows by at most |z_i^T z_j| |lambda_j - lambda_i|.
+constexpr int kOrthNeighbors = 8;
+constexpr double kOrthFixTol = 10.0;  // link when |z_i^T z_j| > 10 m eps (block order m)
+
+__device__ __forceinline__ const double* slot_column(const Dev& v, int64_t w, const Block& bk, const Problem& q) {
+  return v.Z + q.zout + (int64_t)v.spos[w] * q.ldz + (bk.row0 - q.row0);
+}
+
+__device__ __forceinline__ bool slot_has_column(const Dev& v, int64_t w) {
+  const int st = v.state[w];
+  return (st == SLOT_SINGLETON || st == SLOT_FALLBACK || st == SLOT_TRIVIAL) && v.spos[w] >= 0;
+}
+
+__device__ __forceinline__ double warp_dot(const double* a, const double* b, int m, int lane) {
+  double s = 0.0;
+  for (int i = lane; i < m; i += 32) s = fma(a[i], b[i], s);
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
+// One warp per slot: link[w] = largest k <= kOrthNeighbors with
+// |z_w^T z_{w+k}| above the threshold (0 if none).  The per-slot index array
+// sj (no longer needed once the eigenvalues are final) holds the links.
+__global__ void k_orth_links(Dev v) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nslots = v.ctl->nslots;
+  for (int64_t w = gtid() >> 5; w < nslots; w += gstride() >> 5) {
+    int link = 0;
+    if (slot_has_column(v, w)) {
+      const Block bk = v.blk[v.node[v.snode[w]].block];
+      const Problem q = v.prob[bk.prob];
+      const int64_t last = bk.slot0 + (bk.je - bk.js);
+      const double thr = kOrthFixTol * bk.m * kEps;
+      const double* zw = slot_column(v, w, bk, q);
+      for (int k = 1; k <= kOrthNeighbors && w + k <= last; ++k) {
+        if (!slot_has_column(v, w + k)) continue;
+        const double dot = warp_dot(zw, slot_column(v, w + k, bk, q), bk.m, lane);
+        if (fabs(dot) > thr) link = k;
+      }
+    }
+    if (lane == 0) v.sj[w] = link;
+  }
+}
+
+// One warp per block: runs of linked slots, each re-orthogonalised in order.
+__global__ void k_orth_fix(Dev v) {
+  const int lane = threadIdx.x & 31;
+  const int nblocks = v.ctl->nblocks;
+  for (int64_t b = gtid() >> 5; b < nblocks; b += gstride() >> 5) {
+    const Block bk = v.blk[b];
+    if (bk.m < 2 || bk.je < bk.js) continue;
+    const Problem q = v.prob[bk.prob];
+    const int64_t s0 = bk.slot0, s1 = bk.slot0 + (bk.je - bk.js);
+    const int m = bk.m;
+    int64_t w = s0;
+    while (w <= s1) {
+      // next linked slot at or after w, 32 slots per step
+      const int64_t t0 = w + lane;
+      const unsigned msk = __ballot_sync(0xffffffffu, t0 <= s1 && v.sj[t0] != 0);
+      if (!msk) {
+        w += 32;
+        continue;
+      }
+      const int64_t start = w + __ffs(msk) - 1;
+      int64_t reach = start + v.sj[start];
+      for (int64_t t = start + 1; t <= reach && t <= s1; ++t) reach = max(reach, t + (int64_t)v.sj[t]);
+      reach = min(reach, s1);
+      if (lane == 0) diag(v.ctl, DIAG_ORTH_FIX);
+      for (int64_t c = start + 1; c <= reach; ++c) {
+        if (!slot_has_column(v, c)) continue;
+        double* zc = const_cast<double*>(slot_column(v, c, bk, q));
+        for (int pass = 0; pass < 2; ++pass) {
+          for (int64_t p = start; p < c; ++p) {
+            if (!slot_has_column(v, p)) continue;
+            const double* zp = slot_column(v, p, bk, q);
+            const double dot = warp_dot(zc, zp, m, lane);
+            for (int i = lane; i < m; i += 32) zc[i] = fma(-dot, zp[i], zc[i]);
+            __syncwarp();
+          }
+        }
+        const double n2 = warp_dot(zc, zc, m, lane);
+        const double sc = n2 > 0.0 ? 1.0 / sqrt(n2) : 1.0;
+        for (int i = lane; i < m; i += 32) zc[i] *= sc;
+        __syncwarp();
+      }
+      w = reach + 1;
+    }
+  }
+}
+
 // Split problems: columns were placed by the rank of interval midpoints;
 // near-ties across blocks may leave W slightly out of order.  Odd-even
 // transposition passes (one CTA per problem) restore ascending W, moving the
@@ -204,6 +300,10 @@ void launch_vectors(const Dev& v, const Grid& g, cudaStream_t s) {
   count_launch();
   if (v.Z) {
     k_normalize<<<g.nsm * 16, 256, 0, s>>>(v);
+    count_launch();
+    k_orth_links<<<g.nsm * 16, 256, 0, s>>>(v);
+    count_launch();
+    k_orth_fix<<<g.nsm * 4, 128, 0, s>>>(v);
     count_launch();
   }
   k_fix_order<<<g.nsm, 256, 0, s>>>(v);

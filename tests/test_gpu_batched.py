@@ -1,0 +1,122 @@
+"""GPU parity of the batched solver (mrrr_stein_batched): many independent
+problems of uneven sizes in one set of launches, against the CPU oracle per
+problem and against the single-problem path, through the C ABI."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1205_2107_gb300 import api, inputs
+from tests import checks
+
+pytestmark = pytest.mark.gpu
+
+EPS = checks.EPS
+
+
+def _dev(x):
+    return torch.as_tensor(np.asarray(x, dtype=np.float64), device="cuda")
+
+
+def check_problem(d, e, W, Z, il, iu, compare_vectors=True):
+    """Parity of one problem's (W, Z) with the oracle (tolerances of the
+    accuracy goals: 4 n eps ||T||, 20 n eps ||T||, 20 n eps)."""
+    n = len(d)
+    eo = e[:max(n - 1, 0)]
+    if compare_vectors:
+        Wo, Zo = oracle.eigh_tridiagonal(d, eo, il, iu)
+    else:  # eigenvalues only (inverse iteration on long chained clusters is slow)
+        Wo, Zo = oracle.eigvalsh_tridiagonal(d, eo, il, iu), None
+    tn = float(np.max(np.abs(oracle.eigvalsh_tridiagonal(d, eo)))) if n else 0.0
+    Wg = W.cpu().numpy()
+    assert Wg.shape == Wo.shape
+    assert np.all(np.diff(Wg) >= 0)
+    assert np.max(np.abs(Wg - Wo)) <= 4 * n * EPS * tn
+    if Z is None:
+        return
+    res = float(checks.residual_cols(_dev(d), _dev(np.append(e[:max(n - 1, 0)], 0.0)), W, Z).max())
+    assert res <= 20 * n * EPS * tn, f"residual {res:.3e}"
+    assert checks.orthogonality(Z) <= 20 * n * EPS
+    if compare_vectors and n > 1 and il == 1 and iu == n:
+        for sin, bound in checks.subspace_errors(Z.cpu().numpy(), Zo, Wo, tn, n):
+            assert sin <= bound
+
+
+def solve_batch(sizes, seed, il=None, iu=None, vectors=True):
+    d, e, off = inputs.batched_uniform(sizes, seed)
+    lay = api.BatchLayout(sizes, "cuda", il, iu)
+    out = api.eigh_tridiagonal_batched(_dev(d), _dev(e), lay, vectors=vectors)
+    W, Z = out if vectors else (out, None)
+    Ws, Zs = lay.unpack(W, Z) if vectors else (lay.unpack(W), [None] * len(sizes))
+    probs = [(d[off[p]:off[p + 1]], e[off[p]:off[p + 1]]) for p in range(len(sizes))]
+    return lay, probs, Ws, Zs
+
+
+def test_ragged_batch_all_eigenpairs():
+    sizes = [int(x) for x in inputs.batch_sizes(48, seed=3, nmin=1, nmax=300)]
+    sizes[:4] = [1, 2, 3, 300]  # edge sizes in one launch
+    lay, probs, Ws, Zs = solve_batch(sizes, 31)
+    for (d, e), W, Z, n in zip(probs, Ws, Zs, sizes):
+        check_problem(d, e, W, Z, 1, n)
+
+
+def test_batch_subsets_per_problem():
+    sizes = [50, 400, 7, 128, 129, 1000]
+    il = [1, 200, 7, 1, 64, 990]
+    iu = [50, 210, 7, 1, 65, 1000]
+    lay, probs, Ws, Zs = solve_batch(sizes, 17, il, iu)
+    for (d, e), W, Z, a, b in zip(probs, Ws, Zs, il, iu):
+        check_problem(d, e, W, Z, a, b)
+
+
+def test_batch_matches_single_problem_path():
+    sizes = [64, 257, 33, 512]
+    lay, probs, Ws, Zs = solve_batch(sizes, 99)
+    for (d, e), W, Z in zip(probs, Ws, Zs):
+        n = len(d)
+        W1, Z1 = api.eigh_tridiagonal(_dev(d), _dev(e))
+        tn = float(W1.abs().max())
+        assert float((W - W1).abs().max()) <= 4 * n * EPS * tn
+        # the same subspaces: |Z^T Z1| is a permutation-free orthogonal matrix block-diagonally
+        M = (Z.t() @ Z1).abs()
+        assert float((M.max(1).values - 1.0).abs().max()) <= 1e-7
+
+
+def test_batch_with_split_problems_and_values_only():
+    sizes = [40, 40, 40]
+    d, e, off = inputs.batched_uniform(sizes, 5)
+    e[off[0] + 10] = 0.0  # problem 0 splits into two blocks
+    e[off[1]:off[2] - 1:4] = 1e-300  # problem 1 splits into many blocks
+    lay = api.BatchLayout(sizes, "cuda")
+    W = api.eigh_tridiagonal_batched(_dev(d), _dev(e), lay, vectors=False)
+    W2, Z2 = api.eigh_tridiagonal_batched(_dev(d), _dev(e), lay)
+    assert torch.equal(W[:lay.k_total], W2[:lay.k_total])
+    Ws, Zs = lay.unpack(W2, Z2)
+    for p, (W_, Z_) in enumerate(zip(Ws, Zs)):
+        check_problem(d[off[p]:off[p + 1]], e[off[p]:off[p + 1]], W_, Z_, 1, sizes[p])
+
+
+def test_full_size_batch_4096_sampled():
+    """4096 problems, sizes log-uniform in [32, 2048] (the batched workload):
+    every problem checked for residual and orthogonality on the GPU, sampled
+    problems against the oracle."""
+    sizes = [int(x) for x in inputs.batch_sizes()]
+    d, e, off = inputs.batched_uniform(sizes)
+    lay = api.BatchLayout(sizes, "cuda")
+    dt, et = _dev(d), _dev(e)
+    W, Z = api.eigh_tridiagonal_batched(dt, et, lay)
+    Ws, Zs = lay.unpack(W, Z)
+    worst_res = worst_orth = 0.0
+    for p in range(len(sizes)):
+        n = sizes[p]
+        Wp, Zp = Ws[p], Zs[p]
+        tn = float(Wp.abs().max())
+        ep = torch.cat([et[off[p]:off[p + 1] - 1], torch.zeros(1, dtype=torch.float64, device="cuda")])
+        res = float(checks.residual_cols(dt[off[p]:off[p + 1]], ep, Wp, Zp).max()) / (n * EPS * tn)
+        orth = checks.orthogonality(Zp) / (n * EPS)
+        worst_res, worst_orth = max(worst_res, res), max(worst_orth, orth)
+    assert worst_res <= 20 and worst_orth <= 20, (worst_res, worst_orth)
+    rng = np.random.default_rng(0)
+    for p in sorted(set(rng.integers(0, len(sizes), 6).tolist()) | {int(np.argmax(sizes))}):
+        check_problem(d[off[p]:off[p + 1]], e[off[p]:off[p + 1]], Ws[p], Zs[p], 1, sizes[p],
+                      compare_vectors=False)
