@@ -320,6 +320,9 @@ def run_ours(args, rank: int, world: int):
         p, t = oracle_sample(oracle_windows(mats, windows, offset=1), cores)
         cpu = {"value": p / t, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": sample_text(windows, len(mats), cores, t)}
+    side = None
+    if not args.no_side:
+        side = side_by_side(args, dev, flush)
     clocks = clk.summary()
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -331,9 +334,103 @@ def run_ours(args, rank: int, world: int):
             "clocks": clocks, "gpu_launches": launches,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "roofline": roof, "path_roofline": path_roof, "cpu_baseline": cpu,
+            "batched": side["batched"] if side else None, "adjoint": side["adjoint"] if side else None,
             "stages_ms_per_step": {k: v / args.steps for k, v in sorted(stage_ms.items())}}
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def _time_cuda(fn, reps: int, flush) -> float:
+    """Mean milliseconds of fn() over reps runs (CUDA events, L2 flushed before each)."""
+    import torch
+    total = 0.0
+    for _ in range(reps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        e1.synchronize()
+        total += e0.elapsed_time(e1)
+    return total / reps
+
+
+def side_by_side(args, dev, flush):
+    """The batched and adjoint workloads on the same GPU, next to the plain path:
+    4096 problems with n log-uniform in [32, 2048] (one batched solve vs the
+    plain solver looped over a sample of the same problems), and the backward
+    pass of 256 problems of n = 512 (forward solve, then the adjoint)."""
+    import torch
+    from paper_1205_2107_gb300 import api
+    sizes = [int(x) for x in inputs.batch_sizes()]
+    d, e, off = inputs.batched_uniform(sizes)
+    lay = api.BatchLayout(sizes, dev)
+    dt, et = torch.tensor(d, device=dev), torch.tensor(e, device=dev)
+    plan = api.Plan(dev)
+    W = torch.empty(lay.k_total, dtype=torch.float64, device=dev)
+    Z = torch.empty(lay.z_total, dtype=torch.float64, device=dev)
+
+    def batched():
+        api.eigh_tridiagonal_batched(dt, et, lay, plan=plan, check=False, out=(W, Z))
+
+    batched()
+    torch.cuda.synchronize()
+    t_b = _time_cuda(batched, 2, flush)
+    nk_b = sum(n * n for n in sizes)
+    # plain solver looped over every 16th problem (same sizes mix), scaled to the batch
+    sample = list(range(0, len(sizes), 16))
+    pplan = api.Plan(dev)
+
+    def plain_loop():
+        for p in sample:
+            api.eigh_tridiagonal(dt[off[p]:off[p + 1]], et[off[p]:off[p + 1]], plan=pplan, check=False)
+
+    plain_loop()
+    t_p = _time_cuda(plain_loop, 1, flush)
+    n_sample = sum(sizes[p] for p in sample)
+    batched_line = {
+        "workload": "4096 STEPs, n log-uniform in [32, 2048] (seed 2107), d, e iid U[-1,1], all eigenpairs",
+        "ms": t_b, "eigenpairs_per_s": sum(sizes) / (t_b * 1e-3), "matrices_per_s": len(sizes) / (t_b * 1e-3),
+        "path_roofline_frac": 1e3 * PATH_FLOPS_PER_ROW * nk_b / (FP64_PEAK_GFLOPS * 1e9) / t_b,
+        "plain_loop": {"problems": len(sample), "ms": t_p, "eigenpairs_per_s": n_sample / (t_p * 1e-3),
+                       "matrices_per_s": len(sample) / (t_p * 1e-3)},
+    }
+    del W, Z
+    # adjoint: 256 x n = 512, loss sum w_i lambda_i + sum (c_i^T z_i)^2
+    da, ea, wa, Ca = inputs.adjoint_case()
+    batch, n = da.shape
+    alay = api.BatchLayout([n] * batch, dev)
+    dA, eA = torch.tensor(da.reshape(-1), device=dev), torch.tensor(ea.reshape(-1), device=dev)
+    aplan = api.Plan(dev)
+    WA, ZA = api.eigh_tridiagonal_batched(dA, eA, alay, plan=aplan)
+    WA, ZA = WA[:alay.k_total], ZA[:alay.z_total]
+    Ct = torch.tensor(Ca, device=dev).transpose(1, 2)
+    proj = (Ct * ZA.view(batch, n, n)).sum(2)
+    Zbar = (2.0 * Ct * proj[:, :, None]).reshape(-1)
+    Wbar = torch.tensor(wa.reshape(-1), device=dev)
+
+    def forward():
+        api.eigh_tridiagonal_batched(dA, eA, alay, plan=aplan, check=False, out=(WA, ZA))
+
+    def backward():
+        api.eigh_tridiagonal_backward(WA, ZA, Wbar, Zbar, alay, plan=aplan, check=False)
+
+    backward()
+    torch.cuda.synchronize()
+    t_f = _time_cuda(forward, 2, flush)
+    t_bw = _time_cuda(backward, 3, flush)
+    flops_bw = 4.0 * n ** 3 * batch
+    adjoint_line = {
+        "workload": "256 STEPs n=512, d, e iid N(0,1) (seed 1206); loss sum w_i lambda_i + sum (c_i^T z_i)^2",
+        "forward_ms": t_f, "backward_ms": t_bw, "backward_over_forward": t_bw / t_f,
+        "backward_tflops": flops_bw / (t_bw * 1e-3) / 1e12,
+        "backward_frac_of_fp64_peak": flops_bw / (t_bw * 1e-3) / 1e9 / FP64_PEAK_GFLOPS,
+        "fp64_peak_tflops": FP64_PEAK_GFLOPS / 1e3,
+        "fp64_peak_source": "derived FP64 pipe peak (152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz); "
+                            "the backward GEMMs run on the FP64 MMA (mma.sync m8n8k4 f64)",
+    }
+    return {"batched": batched_line, "adjoint": adjoint_line}
 
 
 def main():
@@ -344,6 +441,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target length of the cpu_baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-side", action="store_true", help="skip the batched and adjoint side-by-side legs")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

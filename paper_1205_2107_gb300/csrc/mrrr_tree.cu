@@ -22,11 +22,11 @@ __global__ void k_level_start(Dev v) {
 
 // Boundary flags: a cluster ends after slot w when the (lower bound of the)
 // absolute gap to w+1 is at least tol times the larger magnitude of the two.
-// tol = max(gap_tol, 1 / m) for a block of order m: the vector of a
-// singleton has an error angle of about c eps / relgap with c of order one
-// and no factor m (Eq. errorangle with a residual of a few ulps of the local
-// eigenvalue), while the orthogonality goal scales with m; below m = 1000 the
-// larger threshold keeps c eps / relgap well under m eps.
+// tol = max(gap_tol, 1 / m) for a block of order m.  Eq. errorangle bounds
+// the error angle of a singleton's vector by O(m eps / relgap); on random
+// matrices it behaves like c eps / relgap with c of a few units whatever m
+// is, while the orthogonality goal is 20 m eps, so for small blocks relgap
+// has to exceed about 1/m (below m = 1000 the threshold rises above 1e-3).
 constexpr double kSmallBlockTol = 1.0;
 
 __global__ void k_classify_flags(Dev v, int level) {
