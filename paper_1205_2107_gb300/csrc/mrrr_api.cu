@@ -78,10 +78,10 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-  size_t ctl, prob, blk, node, pool_dl, pool_ul, chunks, lo, hi, gap, wval, znrm2, snode, sj, spos, state, bflag,
+  size_t ctl, prob, blk, node, pool_dl, pool_ul, ilist, lo, hi, gap, wval, znrm2, snode, sj, spos, state, bflag,
       vscr;
   size_t total;
-  int64_t max_blocks, max_nodes, max_slots, pool_rows, vscr_threads, vscr_rows, max_chunks;
+  int64_t max_blocks, max_nodes, max_slots, pool_rows, vscr_threads, vscr_rows;
 };
 
 int vec_threads(const mrrr_plan* p) { return p->nsm * std::max(1, p->opt.vec_blocks_per_sm) * 128; }
@@ -116,8 +116,7 @@ Layout make_layout(const mrrr_plan* p, int batch, int64_t n_total, int64_t k_tot
   L.node = take(sizeof(Node) * (size_t)L.max_nodes);
   L.pool_dl = take(sizeof(double2) * (size_t)L.pool_rows);
   L.pool_ul = take(sizeof(double2) * (size_t)L.pool_rows);
-  L.max_chunks = engine_max_chunks(L.max_slots, L.max_nodes);
-  L.chunks = take(sizeof(Chunk) * (size_t)L.max_chunks);
+  L.ilist = take(sizeof(int64_t) * (size_t)L.max_slots);
 
   L.lo = take(sizeof(double) * (size_t)L.max_slots);
   L.hi = take(sizeof(double) * (size_t)L.max_slots);
@@ -144,9 +143,9 @@ Dev make_dev(const mrrr_plan* p, const Layout& L, void* ws, int batch, const dou
   v.node = reinterpret_cast<Node*>(b + L.node);
   v.rep_dl = reinterpret_cast<double2*>(b + L.pool_dl);
   v.rep_ul = reinterpret_cast<double2*>(b + L.pool_ul);
-  v.chunks = reinterpret_cast<Chunk*>(b + L.chunks);
+  v.ilist = reinterpret_cast<int64_t*>(b + L.ilist);
 
-  v.max_chunks = L.max_chunks;
+  v.max_list = L.max_slots;
   v.pool_cap = L.pool_rows;
   v.max_blocks = (int)std::min<int64_t>(L.max_blocks, INT32_MAX);
   v.max_nodes = (int)L.max_nodes;

@@ -77,12 +77,6 @@ struct RepRow {  // one row of a representation, unpacked
   double D, LLD, l, LD;
 };
 
-// Chunk of the interval engine: slots s0..s1-1 of one node.
-struct Chunk {
-  int node;
-  int pad_;
-  int64_t s0, s1;
-};
 
 // Device control block (first bytes of the workspace).
 struct Ctl {
@@ -100,13 +94,8 @@ struct Ctl {
   int levels;
   int pad_;
   unsigned long long diag[12];  // per-site event counters (see mrrr_info.diag)
-  int nchunks;            // big (CTA) chunks of the current engine launch
-  int chunk_next;         // dynamic counter over big chunks
-  int nsmall;             // small (warp) chunks, stored from the end of the list
-  int small_next;         // dynamic counter over small chunks
-  long long big_slots;    // slots in big nodes (sizes the big chunks)
-  int pad2_;
-  int pad3_;
+  long long nlist;        // intervals in the engine's work list
+  long long list_next;    // next list entry to hand out
 };
 
 // Indices of Ctl::diag (mirrored in mrrr_info.diag).
@@ -134,8 +123,8 @@ struct Dev {
   double2* rep_dl;    // (D, LLD) plane of the representation pool
   double2* rep_ul;    // (l, LD) plane
   int64_t pool_cap;   // rows
-  Chunk* chunks;      // work list of the interval engine
-  int64_t max_chunks;
+  int64_t* ilist;     // work list of the interval engine (slot indices)
+  int64_t max_list;
 
   int max_blocks;
   int max_nodes;

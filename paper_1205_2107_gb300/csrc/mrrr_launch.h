@@ -69,7 +69,6 @@ void launch_level_children(const Dev& v, int level, const Grid& g, cudaStream_t 
 // interval engine: mode 0 root bisection, 1 cluster pre-refinement in the
 // parent, 2 refinement in the child (see mrrr_engine.cu)
 void launch_engine(const Dev& v, int mode, const Grid& g, cudaStream_t s);
-int64_t engine_max_chunks(int64_t max_slots, int64_t max_nodes);
 
 // eigenvectors (twisted factorization + Rayleigh-quotient correction),
 // normalisation and ordering of split problems
