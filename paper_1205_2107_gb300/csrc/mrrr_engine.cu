@@ -4,8 +4,9 @@
 // are refined to high relative accuracy on the cluster's new RRR).
 //
 // One launch works on one list of intervals (slot indices), built per mode
-// by k_list.  The multisection width T (a power of two, 1..32) follows from
-// the list length and the number of resident lanes: with few intervals each
+// by k_list and split into long intervals (many halvings to go) and short
+// ones; the long ones run first.  The multisection width T (a power of two,
+// 1..32) follows from each part's length and the number of resident lanes: with few intervals each
 // gets T lanes that evaluate T interior points per pass over the
 // representation (log2(T+1) bits per pass instead of one, which shortens the
 // chain of dependent passes); with many intervals T = 1 and no work is
@@ -69,10 +70,36 @@ __global__ void k_list_reset(Dev v) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     v.ctl->nlist = 0;
     v.ctl->list_next = 0;
+    v.ctl->nlist2 = 0;
+    v.ctl->list_next2 = 0;
   }
 }
 
-// Compaction of the wanted slots into the list (warp-aggregated appends).
+template <int MODE>
+__device__ __forceinline__ double mode_rtol(const Dev& v) {
+  return MODE == MODE_ROOT || MODE == MODE_REFINE ? v.rtol : MODE == MODE_FINAL ? 2.0 * kEps : v.rtol_cluster;
+}
+
+constexpr double kLongBits = 12.0;  // bisection steps above which an interval is "long"
+
+// Whether the interval of slot w still needs more than kLongBits halvings
+// (estimated from its current bracket; ROOT brackets are always long).
+template <int MODE>
+__device__ __forceinline__ bool slot_is_long(const Dev& v, int64_t w) {
+  if (MODE == MODE_ROOT) return true;
+  double lo = v.lo[w], hi = v.hi[w];
+  if (MODE == MODE_REFINE) {
+    const double sig = v.node[v.snode[w]].sigma_rel;
+    const double delta = 16.0 * kEps * fmax(fabs(lo), fabs(hi));
+    lo = lo - sig - delta;
+    hi = hi - sig + delta;
+  }
+  const double goal = mode_rtol<MODE>(v) * fmax(fabs(lo), fabs(hi));
+  return hi - lo > ldexp(goal, (int)kLongBits);
+}
+
+// Compaction of the wanted slots into the list (warp-aggregated appends):
+// long intervals from the front (nlist), short ones from the back (nlist2).
 template <int MODE>
 __global__ void k_list(Dev v) {
   const int lane = threadIdx.x & 31;
@@ -81,22 +108,24 @@ __global__ void k_list(Dev v) {
   for (int64_t w0 = gtid() - lane; w0 < nslots; w0 += gstride()) {
     const int64_t w = w0 + lane;
     const bool want = w < nslots && slot_in_mode<MODE>(v, w, level_begin);
-    const unsigned mask = __ballot_sync(0xffffffffu, want);
-    if (!mask) continue;
-    long long base = 0;
-    if (lane == 0)
-      base = (long long)atomicAdd((unsigned long long*)&v.ctl->nlist, (unsigned long long)__popc(mask));
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if (want) {
-      const long long at = base + __popc(mask & ((1u << lane) - 1u));
+    const bool lng = want && slot_is_long<MODE>(v, w);
+    const unsigned ml = __ballot_sync(0xffffffffu, lng);
+    const unsigned ms = __ballot_sync(0xffffffffu, want && !lng);
+    if (!(ml | ms)) continue;
+    unsigned long long bl = 0, bs = 0;
+    if (lane == 0 && ml) bl = atomicAdd((unsigned long long*)&v.ctl->nlist, (unsigned long long)__popc(ml));
+    if (lane == 0 && ms) bs = atomicAdd((unsigned long long*)&v.ctl->nlist2, (unsigned long long)__popc(ms));
+    bl = __shfl_sync(0xffffffffu, bl, 0);
+    bs = __shfl_sync(0xffffffffu, bs, 0);
+    const unsigned below = (1u << lane) - 1u;
+    if (lng) {
+      const long long at = (long long)bl + __popc(ml & below);
       if (at < v.max_list) v.ilist[at] = w;
+    } else if (want) {
+      const long long at = (long long)bs + __popc(ms & below);
+      if (at < v.max_list) v.ilist[v.max_list - 1 - at] = w;
     }
   }
-}
-
-template <int MODE>
-__device__ __forceinline__ double mode_rtol(const Dev& v) {
-  return MODE == MODE_ROOT || MODE == MODE_REFINE ? v.rtol : MODE == MODE_FINAL ? 2.0 * kEps : v.rtol_cluster;
 }
 
 // Per-interval state, replicated in every lane of the interval's group.
@@ -241,62 +270,77 @@ __device__ __forceinline__ int lane_count(const double2* __restrict__ dl, int m,
   return neg;
 }
 
+// Multisection width for a list of nlist intervals: the largest power of
+// two T <= 32 with 2 T nlist <= lanes_total.
+__device__ __forceinline__ int width_for(long long nlist, long long lanes_total) {
+  int T = 1;
+  while (T < 32 && 2LL * T * nlist <= lanes_total) T *= 2;
+  return T;
+}
+
+// Phase 0 drains the long intervals (front of the list), phase 1 the short
+// ones (back of the list), each with the width that its own length allows;
+// a warp moves on to phase 1 as soon as the long list is exhausted for it.
 template <int MODE>
 __global__ void __launch_bounds__(kEngThreads, kEngCtasPerSm) k_engine(Dev v) {
   const int lane = threadIdx.x & 31;
-  const long long nlist = min(v.ctl->nlist, (long long)v.max_list);
-  if (nlist == 0) return;
+  const long long nlong = min(v.ctl->nlist, (long long)v.max_list);
+  const long long nshort = min(v.ctl->nlist2, (long long)v.max_list - nlong);
   const long long lanes_total = (long long)gridDim.x * blockDim.x;
-  int T = 1;
-  while (T < 32 && 2LL * T * nlist <= lanes_total) T *= 2;
-  const int pt = lane % T, leader = lane - pt;
-  const unsigned gbits = T == 32 ? 0xffffffffu : (((1u << T) - 1u) << leader);
   const double rtol = mode_rtol<MODE>(v);
   const int maxsteps = v.max_bisect;
-
-  Iv q{};
-  bool have = false, exhausted = false;
-  for (;;) {
-    // groups without an interval take the next ones from the list; an
-    // interval already converged on entry is finished at once
-    while (__any_sync(0xffffffffu, !have && !exhausted)) {
-      long long item = 0;
-      if (!have && !exhausted && pt == 0) item = (long long)atomicAdd((unsigned long long*)&v.ctl->list_next, 1ull);
-      item = __shfl_sync(0xffffffffu, item, leader);
-      if (!have && !exhausted) {
-        if (item >= nlist) {
-          exhausted = true;
-        } else {
-          iv_load<MODE>(v, v.ilist[item], q);
-          if (q.phase == PH_BISECT && converged(q.lo, q.hi, rtol, q.atol)) {
-            if (pt == 0) {
-              v.lo[q.slot] = q.lo;
-              v.hi[q.slot] = q.hi;
-            }
+  for (int phase = 0; phase < 2; ++phase) {
+    const long long nlist = phase == 0 ? nlong : nshort;
+    if (nlist == 0) continue;
+    unsigned long long* next = phase == 0 ? (unsigned long long*)&v.ctl->list_next
+                                          : (unsigned long long*)&v.ctl->list_next2;
+    const int T = width_for(nlist, lanes_total);
+    const int pt = lane % T, leader = lane - pt;
+    const unsigned gbits = T == 32 ? 0xffffffffu : (((1u << T) - 1u) << leader);
+    Iv q{};
+    bool have = false, exhausted = false;
+    for (;;) {
+      // groups without an interval take the next ones from the list; an
+      // interval already converged on entry is finished at once
+      while (__any_sync(0xffffffffu, !have && !exhausted)) {
+        long long item = 0;
+        if (!have && !exhausted && pt == 0) item = (long long)atomicAdd(next, 1ull);
+        item = __shfl_sync(0xffffffffu, item, leader);
+        if (!have && !exhausted) {
+          if (item >= nlist) {
+            exhausted = true;
           } else {
-            have = true;
+            iv_load<MODE>(v, v.ilist[phase == 0 ? item : v.max_list - 1 - item], q);
+            if (q.phase == PH_BISECT && converged(q.lo, q.hi, rtol, q.atol)) {
+              if (pt == 0) {
+                v.lo[q.slot] = q.lo;
+                v.hi[q.slot] = q.hi;
+              }
+            } else {
+              have = true;
+            }
           }
         }
       }
-    }
-    if (!__any_sync(0xffffffffu, have)) break;
-    double tau = 0.0;
-    bool act = have;
-    if (act) act = iv_tau(q, T, pt, tau);
-    int m_all = act ? q.m : 0;
-    for (int o = 16; o; o >>= 1) m_all = max(m_all, __shfl_xor_sync(0xffffffffu, m_all, o));
-    const int neg = lane_count(q.dl, q.m, m_all, tau, q.pivexp, q.pivmin, act);
-    // the group's counts: first point with count >= j, and points 0 and 1
-    const unsigned ge = __ballot_sync(0xffffffffu, act && neg >= q.j) & gbits;
-    const int kfirst = ge ? (__ffs(ge) - 1 - leader) : T;
-    const int c0 = __shfl_sync(0xffffffffu, neg, leader);
-    const int c1 = __shfl_sync(0xffffffffu, neg, T >= 2 ? leader + 1 : leader);
-    if (have && iv_update<MODE>(v, T, rtol, maxsteps, kfirst, c0, c1, q)) {
-      if (pt == 0) {
-        v.lo[q.slot] = q.lo;
-        v.hi[q.slot] = q.hi;
+      if (!__any_sync(0xffffffffu, have)) break;
+      double tau = 0.0;
+      bool act = have;
+      if (act) act = iv_tau(q, T, pt, tau);
+      int m_all = act ? q.m : 0;
+      for (int o = 16; o; o >>= 1) m_all = max(m_all, __shfl_xor_sync(0xffffffffu, m_all, o));
+      const int neg = lane_count(q.dl, q.m, m_all, tau, q.pivexp, q.pivmin, act);
+      // the group's counts: first point with count >= j, and points 0 and 1
+      const unsigned ge = __ballot_sync(0xffffffffu, act && neg >= q.j) & gbits;
+      const int kfirst = ge ? (__ffs(ge) - 1 - leader) : T;
+      const int c0 = __shfl_sync(0xffffffffu, neg, leader);
+      const int c1 = __shfl_sync(0xffffffffu, neg, T >= 2 ? leader + 1 : leader);
+      if (have && iv_update<MODE>(v, T, rtol, maxsteps, kfirst, c0, c1, q)) {
+        if (pt == 0) {
+          v.lo[q.slot] = q.lo;
+          v.hi[q.slot] = q.hi;
+        }
+        have = false;
       }
-      have = false;
     }
   }
 }

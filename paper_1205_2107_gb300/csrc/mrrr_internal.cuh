@@ -94,8 +94,10 @@ struct Ctl {
   int levels;
   int pad_;
   unsigned long long diag[12];  // per-site event counters (see mrrr_info.diag)
-  long long nlist;        // intervals in the engine's work list
-  long long list_next;    // next list entry to hand out
+  long long nlist;        // long intervals in the engine's work list (front)
+  long long list_next;    // next long entry to hand out
+  long long nlist2;       // short intervals (back of the list)
+  long long list_next2;   // next short entry to hand out
 };
 
 // Indices of Ctl::diag (mirrored in mrrr_info.diag).
