@@ -10,9 +10,8 @@
 // gets T lanes that evaluate T interior points per pass over the
 // representation (log2(T+1) bits per pass instead of one, which shortens the
 // chain of dependent passes); with many intervals T = 1 and no work is
-// duplicated.  A warp holds 32/T lane groups; a group that finishes its
-// interval takes the next one from the list (atomic counter), so lanes stay
-// busy until the list is exhausted.  Every lane streams its node's (D, LLD)
+// duplicated.  A warp holds 32/T lane groups and takes 32/T consecutive
+// list entries at a time (atomic counter) once all its groups are done.  Every lane streams its node's (D, LLD)
 // rows from L1/L2 with a register prefetch; the lanes of a group read the
 // same rows.  The Sturm counts are the division-free recurrence of
 // count_step().
@@ -297,28 +296,32 @@ __global__ void __launch_bounds__(kEngThreads, kEngCtasPerSm) k_engine(Dev v) {
     const int T = width_for(nlist, lanes_total);
     const int pt = lane % T, leader = lane - pt;
     const unsigned gbits = T == 32 ? 0xffffffffu : (((1u << T) - 1u) << leader);
+    const int groups = 32 / T, grp = lane / T;
     Iv q{};
     bool have = false, exhausted = false;
     for (;;) {
-      // groups without an interval take the next ones from the list; an
+      // when every group of the warp is done, the warp takes the next
+      // `groups` consecutive list entries (neighbouring slots: the same node
+      // or problem, so the lanes share row lengths and often rows); an
       // interval already converged on entry is finished at once
-      while (__any_sync(0xffffffffu, !have && !exhausted)) {
-        long long item = 0;
-        if (!have && !exhausted && pt == 0) item = (long long)atomicAdd(next, 1ull);
-        item = __shfl_sync(0xffffffffu, item, leader);
-        if (!have && !exhausted) {
-          if (item >= nlist) {
-            exhausted = true;
-          } else {
-            iv_load<MODE>(v, v.ilist[phase == 0 ? item : v.max_list - 1 - item], q);
-            if (q.phase == PH_BISECT && converged(q.lo, q.hi, rtol, q.atol)) {
-              if (pt == 0) {
-                v.lo[q.slot] = q.lo;
-                v.hi[q.slot] = q.hi;
-              }
-            } else {
-              have = true;
+      while (!exhausted && !__any_sync(0xffffffffu, have)) {
+        long long base = 0;
+        if (lane == 0) base = (long long)atomicAdd(next, (unsigned long long)groups);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= nlist) {
+          exhausted = true;
+          break;
+        }
+        const long long item = base + grp;
+        if (item < nlist) {
+          iv_load<MODE>(v, v.ilist[phase == 0 ? item : v.max_list - 1 - item], q);
+          if (q.phase == PH_BISECT && converged(q.lo, q.hi, rtol, q.atol)) {
+            if (pt == 0) {
+              v.lo[q.slot] = q.lo;
+              v.hi[q.slot] = q.hi;
             }
+          } else {
+            have = true;
           }
         }
       }
