@@ -66,7 +66,8 @@ typedef struct mrrr_options {
   int max_bisect_steps;    /* per interval and pass (256) */
   int reserved1;
   int threads_per_block;   /* CUDA block size of the interval kernels (128) */
-  int vec_blocks_per_sm;   /* resident blocks per SM of the eigenvector kernel (4) */
+  int vec_blocks_per_sm;   /* 128-thread blocks per SM of the eigenvector kernel (8);
+                              capped by the number of eigenpairs */
   int reserved0;
   int64_t max_nodes;       /* capacity of the cluster-node table (0 = automatic) */
   int64_t pool_rows;       /* capacity of the child-representation pool in rows of

@@ -84,7 +84,13 @@ struct Layout {
   int64_t max_blocks, max_nodes, max_slots, pool_rows, vscr_threads, vscr_rows;
 };
 
-int vec_threads(const mrrr_plan* p) { return p->nsm * std::max(1, p->opt.vec_blocks_per_sm) * 128; }
+// Threads of the eigenvector kernel (one vector at a time each): enough
+// resident warps to hide the division chains, but no more than there are
+// eigenpairs (each thread owns n_max doubles of scratch).
+int64_t vec_threads(const mrrr_plan* p, int64_t max_slots) {
+  const int64_t cap = (int64_t)p->nsm * std::max(1, p->opt.vec_blocks_per_sm) * 128;
+  return std::max<int64_t>(128, std::min(cap, (max_slots + 127) / 128 * 128));
+}
 
 Layout make_layout(const mrrr_plan* p, int batch, int64_t n_total, int64_t k_total, int n_max) {
   Layout L{};
@@ -102,7 +108,7 @@ Layout make_layout(const mrrr_plan* p, int batch, int64_t n_total, int64_t k_tot
     pool_child = std::min(want, cap);
   }
   L.pool_rows = n_total + pool_child;
-  L.vscr_threads = vec_threads(p);
+  L.vscr_threads = vec_threads(p, L.max_slots);
   L.vscr_rows = std::max(n_max, 1);
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -185,7 +191,7 @@ Grid make_grid(const mrrr_plan* p, int64_t max_slots) {
   g.tpb = std::max(32, std::min(1024, p->opt.threads_per_block));
   int64_t want = (max_slots + g.tpb - 1) / g.tpb;
   g.slot_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)p->nsm * 32));
-  g.vec_blocks = p->nsm * std::max(1, p->opt.vec_blocks_per_sm);
+  g.vec_blocks = (int)(vec_threads(p, max_slots) / 128);
   return g;
 }
 
@@ -246,7 +252,7 @@ mrrr_status mrrr_options_default(mrrr_options* opt) {
   opt->max_depth = 64;
   opt->max_bisect_steps = 256;
   opt->threads_per_block = 128;
-  opt->vec_blocks_per_sm = 1;
+  opt->vec_blocks_per_sm = 8;
   opt->cluster_rtol = 0x1p-40;
   opt->root_perturb = 64.0;
   return MRRR_OK;

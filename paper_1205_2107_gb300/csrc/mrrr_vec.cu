@@ -24,23 +24,42 @@ namespace mrrr {
 
 namespace {
 
+constexpr int kRowAhead = 4;  // representation rows loaded ahead of the qd recurrences
+
 // A: L+ (stride as), B: s then U- (stride bs), z: output (stride zs; may alias A).
-// Returns the Sturm count (negative pivots of the stationary part).
+// Returns the Sturm count (negative pivots of the stationary part).  The
+// representation rows are read kRowAhead rows ahead of the recurrences, whose
+// dependent chains (a division per row) do not wait on the loads.
 __device__ int twisted_solve(const double2* __restrict__ dl, const double2* __restrict__ ul, int m, double lam,
                              double pivmin,
                              double* A, int64_t as, double* B, int64_t bs, double* z, int64_t zs,
                              int& r, double& gamma, double& norm2) {
   int negc = 0;
   double s = -lam;
-  for (int i = 0; i < m - 1; ++i) {
-    const RepRow R = rep_row(dl, ul, i);
-    double dp = R.D + s;
-    if (fabs(dp) < pivmin) dp = -pivmin;
-    negc += (dp < 0.0);
-    double lp = R.LD / dp;
-    A[i * as] = lp;
-    B[i * bs] = s;
-    s = fma(lp, R.l * s, -lam);
+  double2 pd[kRowAhead], pu[kRowAhead];
+#pragma unroll
+  for (int u = 0; u < kRowAhead; ++u) {
+    pd[u] = u < m - 1 ? __ldg(dl + u) : make_double2(0.0, 0.0);
+    pu[u] = u < m - 1 ? __ldg(ul + u) : make_double2(0.0, 0.0);
+  }
+  for (int i0 = 0; i0 < m - 1; i0 += kRowAhead) {
+#pragma unroll
+    for (int u = 0; u < kRowAhead; ++u) {
+      const int i = i0 + u;
+      const double2 xd = pd[u], xu = pu[u];
+      const int inext = i + kRowAhead;
+      pd[u] = inext < m - 1 ? __ldg(dl + inext) : make_double2(0.0, 0.0);
+      pu[u] = inext < m - 1 ? __ldg(ul + inext) : make_double2(0.0, 0.0);
+      if (i < m - 1) {
+        double dp = xd.x + s;
+        if (fabs(dp) < pivmin) dp = -pivmin;
+        negc += (dp < 0.0);
+        const double lp = xu.y / dp;  // LD / D+
+        A[i * as] = lp;
+        B[i * bs] = s;
+        s = fma(lp, xu.x * s, -lam);  // L+ l s - lambda
+      }
+    }
   }
   {
     double dp = dl[m - 1].x + s;
@@ -53,20 +72,35 @@ __device__ int twisted_solve(const double2* __restrict__ dl, const double2* __re
   double best = fabs(g);
   r = m - 1;
   gamma = g;
-  for (int i = m - 2; i >= 0; --i) {
-    const RepRow R = rep_row(dl, ul, i);
-    double dm = R.LLD + p;
-    if (fabs(dm) < pivmin) dm = -pivmin;
-    double t = R.D / dm;
-    double um = R.l * t;
-    p = fma(p, t, -lam);
-    g = B[i * bs] + p + lam;
-    if (fabs(g) <= best) {
-      best = fabs(g);
-      r = i;
-      gamma = g;
+#pragma unroll
+  for (int u = 0; u < kRowAhead; ++u) {
+    const int i = m - 2 - u;
+    pd[u] = i >= 0 ? __ldg(dl + i) : make_double2(0.0, 0.0);
+    pu[u] = i >= 0 ? __ldg(ul + i) : make_double2(0.0, 0.0);
+  }
+  for (int i0 = m - 2; i0 >= 0; i0 -= kRowAhead) {
+#pragma unroll
+    for (int u = 0; u < kRowAhead; ++u) {
+      const int i = i0 - u;
+      const double2 xd = pd[u], xu = pu[u];
+      const int inext = i - kRowAhead;
+      pd[u] = inext >= 0 ? __ldg(dl + inext) : make_double2(0.0, 0.0);
+      pu[u] = inext >= 0 ? __ldg(ul + inext) : make_double2(0.0, 0.0);
+      if (i >= 0) {
+        double dm = xd.y + p;  // LLD + p
+        if (fabs(dm) < pivmin) dm = -pivmin;
+        const double t = xd.x / dm;  // D / D-
+        const double um = xu.x * t;  // l D / D-
+        p = fma(p, t, -lam);
+        g = B[i * bs] + p + lam;
+        if (fabs(g) <= best) {
+          best = fabs(g);
+          r = i;
+          gamma = g;
+        }
+        B[i * bs] = um;
+      }
     }
-    B[i * bs] = um;
   }
   double zi = 1.0, n2 = 1.0;
   z[(int64_t)r * zs] = 1.0;
