@@ -209,57 +209,73 @@ __global__ void k_childrep_first(Dev v) {
       set_child(v, id, c, p, base, sigma, R);
     } else {
       c.rep = base;
-      c.pad_ = 1;  // phase 2
+      c.pad_ = 1;           // phase 2
+      c.sigma_rel = gd;     // growth of the first candidate, for phase 2
       v.node[id] = c;
     }
   }
 }
 
-// Phase 2, one warp per node whose first candidate failed: the lanes
-// evaluate all 2 x kShiftTries candidate shifts at once (growth only), the
-// first candidate in the order of child_shift whose growth max|D+| is at most
-// 8 spdiam is taken, else the one with the smallest growth (counted in the
-// diagnostics); the chosen transform is then recomputed with stores into the
-// rows reserved in phase 1.
+// Phase 2, for nodes whose first candidate failed: a group of 8 lanes per
+// node (4 nodes per warp) evaluates 8 further candidates spread over the
+// ladder of child_shift (growth only); the first candidate in ladder order
+// whose growth max|D+| is at most 8 spdiam is taken, else the one with the
+// smallest growth among these and the first candidate (counted in the
+// diagnostics).  The chosen transform is then recomputed with stores into
+// the rows reserved in phase 1.
+constexpr int kPhase2Group = 8;
+__constant__ int kPhase2Cands[kPhase2Group] = {1, 2, 3, 4, 8, 9, 18, 19};
+
 __global__ void k_childrep(Dev v) {
   const int lane = threadIdx.x & 31;
+  const int sub = lane / kPhase2Group, gl = lane % kPhase2Group, leader = sub * kPhase2Group;
+  const int per_warp = 32 / kPhase2Group;
   const int64_t warp = gtid() >> 5, nwarps = gstride() >> 5;
   const int begin = v.ctl->level_begin;
   const int end = min(v.ctl->nodes, v.max_nodes);
-  for (int64_t id = begin + warp; id < end; id += nwarps) {
-    const Node c = v.node[id];
-    if (c.pad_ != 1) continue;
-    const Node p = v.node[c.parent];
-    const int m = v.blk[c.block].m;
-    const double2* pdl = v.rep_dl + p.rep;
-    const double2* pul = v.rep_ul + p.rep;
-    const double lo_f = v.lo[c.first], hi_l = v.hi[c.last];
-    const double bound = 8.0 * c.spdiam;
-    double sigma = lo_f, g = INFINITY;
-    if (lane < 2 * kShiftTries) {
-      sigma = child_shift(lane, lo_f, hi_l, p.pivmin);
-      g = dstqds_child<false>(pdl, pul, nullptr, nullptr, m, sigma, p.pivmin);
+  for (int64_t id0 = begin + warp * per_warp; id0 < end; id0 += nwarps * per_warp) {
+    const int64_t id = id0 + sub;
+    Node c{};
+    bool mine = id < end;
+    if (mine) {
+      c = v.node[id];
+      mine = c.pad_ == 1;
     }
-    const unsigned okmask = __ballot_sync(0xffffffffu, g <= bound);
+    double g = INFINITY, sigma = 0.0;
+    int cand = 0;
+    Node p{};
+    if (mine) {
+      p = v.node[c.parent];
+      const int m = v.blk[c.block].m;
+      cand = kPhase2Cands[gl];
+      sigma = child_shift(cand, v.lo[c.first], v.hi[c.last], p.pivmin);
+      g = dstqds_child<false>(v.rep_dl + p.rep, v.rep_ul + p.rep, nullptr, nullptr, m, sigma, p.pivmin);
+    }
+    const unsigned gbits = 0xffu << leader;
+    const bool ok = mine && g <= 8.0 * c.spdiam;
+    const unsigned okmask = __ballot_sync(0xffffffffu, ok) & gbits;
+    // smallest growth in the group, lowest candidate on ties
+    double bg = g;
+    int bc = cand;
+    for (int o = kPhase2Group / 2; o; o >>= 1) {
+      const double og = __shfl_xor_sync(0xffffffffu, bg, o);
+      const int oc = __shfl_xor_sync(0xffffffffu, bc, o);
+      if (og < bg || (og == bg && oc < bc)) bg = og, bc = oc;
+    }
+    if (!mine || gl != 0) continue;
+    const int m = v.blk[c.block].m;
     int pick;
     if (okmask) {
-      pick = __ffs(okmask) - 1;
-    } else {  // smallest growth, lowest lane on ties
-      double bg = g;
-      int bl = lane;
-      for (int o = 16; o; o >>= 1) {
-        double og = __shfl_xor_sync(0xffffffffu, bg, o);
-        int ol = __shfl_xor_sync(0xffffffffu, bl, o);
-        if (og < bg || (og == bg && ol < bl)) bg = og, bl = ol;
-      }
-      pick = bl;
-      if (lane == 0) diag(v.ctl, DIAG_CHILD_GROWTH);
+      pick = kPhase2Cands[__ffs(okmask) - 1 - leader];
+    } else {
+      // the first candidate's growth was kept in sigma_rel by phase 1
+      pick = c.sigma_rel <= bg ? 0 : bc;
+      diag(v.ctl, DIAG_CHILD_GROWTH);
     }
-    sigma = __shfl_sync(0xffffffffu, sigma, pick);
-    if (lane == 0) {
-      const double R = dstqds_child<true>(pdl, pul, v.rep_dl + c.rep, v.rep_ul + c.rep, m, sigma, p.pivmin);
-      set_child(v, id, c, p, c.rep, sigma, R);
-    }
+    const double sig = child_shift(pick, v.lo[c.first], v.hi[c.last], p.pivmin);
+    const double R =
+        dstqds_child<true>(v.rep_dl + p.rep, v.rep_ul + p.rep, v.rep_dl + c.rep, v.rep_ul + c.rep, m, sig, p.pivmin);
+    set_child(v, id, c, p, c.rep, sig, R);
   }
 }
 
