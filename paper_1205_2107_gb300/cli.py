@@ -5,7 +5,8 @@
 Families are the seeded generators of ``inputs``: uniform (d, e iid
 U[-1, 1]), normal, toeplitz (d = 2, e = -1), wilkinson (W+), glued (copies of
 W21+ glued by 1e-10; --n is the number of copies), clement, large (d U[0,1],
-e U[0, 1e-2]).  Prints the stage profile of the last solve as one JSON line.
+e U[0, 1e-2]); batch (--n problems of sizes log-uniform in [32, 2048], one
+batched solve).  Prints the stage profile of the last solve as one JSON line.
 """
 from __future__ import annotations
 
@@ -28,9 +29,34 @@ FAMILIES = {
 }
 
 
+def run_batch(args, dev):
+    """--n problems with sizes log-uniform in [32, 2048], d, e iid U[-1,1]."""
+    sizes = [int(x) for x in inputs.batch_sizes(args.n, args.seed)]
+    d, e, _ = inputs.batched_uniform(sizes, args.seed)
+    lay = api.BatchLayout(sizes, dev)
+    dd, ee = torch.tensor(d, device=dev), torch.tensor(e, device=dev)
+    plan = api.Plan(dev)
+    plan.set_timing(True)
+    times = []
+    for _ in range(args.repeat):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        api.eigh_tridiagonal_batched(dd, ee, lay, plan=plan, vectors=not args.values_only, check=False)
+        ev1.record()
+        ev1.synchronize()
+        times.append(ev0.elapsed_time(ev1))
+    info = plan.info()
+    prof = plan.profile()
+    print(json.dumps({"family": "batch", "problems": len(sizes), "n_total": lay.n_total, "ms": times,
+                      "status": info["status"], "depth": info["depth"], "nodes": info["nodes"],
+                      "launches": prof["launches"], "stages_ms": prof["stages"]}))
+    if info["status"] != 0:
+        raise SystemExit(f"solver status {info['status']}")
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
-    ap.add_argument("--family", choices=sorted(FAMILIES), default="uniform")
+    ap.add_argument("--family", choices=sorted(FAMILIES) + ["batch"], default="uniform")
     ap.add_argument("--n", type=int, default=1000)
     ap.add_argument("--seed", type=int, default=1205)
     ap.add_argument("--il", type=int, default=None)
@@ -38,8 +64,10 @@ def main(argv=None):
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--values-only", action="store_true")
     args = ap.parse_args(argv)
-    d, e = FAMILIES[args.family](args.n, args.seed)
     dev = torch.device("cuda", torch.cuda.current_device())
+    if args.family == "batch":
+        return run_batch(args, dev)
+    d, e = FAMILIES[args.family](args.n, args.seed)
     dd = torch.tensor(d, device=dev)
     ee = torch.tensor(np.append(e, 0.0), device=dev)
     plan = api.Plan(dev)
