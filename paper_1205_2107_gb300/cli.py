@@ -41,7 +41,7 @@ def run_batch(args, dev):
     for _ in range(args.repeat):
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record()
-        api.eigh_tridiagonal_batched(dd, ee, lay, plan=plan, vectors=not args.values_only, check=False)
+        api.eigh_tridiagonal_batched(dd, ee, lay, plan=plan, vectors=not args.values_only)
         ev1.record()
         ev1.synchronize()
         times.append(ev0.elapsed_time(ev1))
@@ -76,7 +76,7 @@ def main(argv=None):
     for _ in range(args.repeat):
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record()
-        api.eigh_tridiagonal(dd, ee, args.il, args.iu, plan=plan, vectors=not args.values_only, check=False)
+        api.eigh_tridiagonal(dd, ee, args.il, args.iu, plan=plan, vectors=not args.values_only)
         ev1.record()
         ev1.synchronize()
         times.append(ev0.elapsed_time(ev1))
