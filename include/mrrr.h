@@ -47,9 +47,10 @@ typedef enum mrrr_status {
   MRRR_ERR_ARG = 1,        /* invalid argument (size, range, null pointer) */
   MRRR_ERR_WORKSPACE = 2,  /* workspace missing or smaller than required   */
   MRRR_ERR_NONFINITE = 3,  /* d or e holds NaN or Inf (found on the GPU)   */
-  MRRR_ERR_NOCONV = 4,     /* an iteration hit its cap (bisection, RQI)    */
+  MRRR_ERR_NOCONV = 4,     /* an iteration hit its cap (bisection)         */
   MRRR_ERR_QUEUE = 5,      /* cluster-node table or representation pool full */
-  MRRR_ERR_TIMEOUT = 6,    /* a bounded device wait gave up                */
+  MRRR_ERR_TIMEOUT = 6,    /* reserved (bounded device waits); no kernel of
+                              this version waits on another                */
   MRRR_ERR_CUDA = 7,       /* a CUDA runtime call failed                   */
   MRRR_ERR_NOTIMPL = 8     /* option combination not implemented           */
 } mrrr_status;
