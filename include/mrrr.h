@@ -65,11 +65,14 @@ typedef struct mrrr_options {
   int max_depth;           /* cluster-tree depth limit (64); deeper clusters take the
                               documented fallback and are counted in mrrr_info */
   int max_bisect_steps;    /* per interval and pass (256) */
-  int reserved1;
+  int engine_blocks_per_sm; /* 256-thread CTAs per SM of the interval engine (2; 1 or 2) */
   int threads_per_block;   /* CUDA block size of the interval kernels (128) */
   int vec_blocks_per_sm;   /* 128-thread blocks per SM of the eigenvector kernel (8);
                               capped by the number of eigenpairs */
-  int reserved0;
+  int use_graph;           /* 1: the solve's launches (levels driven on the device, no host
+                              synchronisation) are captured once into a CUDA graph per call
+                              signature and replayed; 0: launched directly, the host reads
+                              the new-cluster count after each level (default) */
   int64_t max_nodes;       /* capacity of the cluster-node table (0 = automatic) */
   int64_t pool_rows;       /* capacity of the child-representation pool in rows of
                               32 bytes (0 = automatic) */
@@ -79,6 +82,8 @@ typedef struct mrrr_options {
   double root_perturb;     /* relative size, in units of eps, of the seeded random
                               perturbation of each root representation entry (64,
                               at most m/8 for a block of order m; negative = none) */
+  double width_scale;      /* scales the resident lanes when the engine chooses its
+                              multisection width (1.0; larger = more points per interval) */
 } mrrr_options;
 
 /* Counters reported by mrrr_get_status (device values after the last solve). */
@@ -155,6 +160,31 @@ mrrr_status mrrr_stein_batched(mrrr_plan* plan, int batch, const int64_t* d_off,
                                const int64_t* w_off, double* Z, const int64_t* z_off, int64_t n_total,
                                int64_t k_total, int n_max, void* workspace, size_t ws_bytes,
                                mrrr_stream stream);
+
+/*
+ * mrrr_autotune_batched: choose the launch shape of the batched solver for
+ * one batch layout by timing it.  Not in the paper (a scheduling aid for
+ * the batched pattern).  Candidates: engine_blocks_per_sm in {2, 1} x
+ * width_scale (points per interval of the multisection) in {1, 0.5, 2};
+ * each solves the batch once (after one untimed warm-up solve) with CUDA
+ * events on stream.  The fastest becomes the plan's setting (the plan's
+ * CUDA graph, if any, is rebuilt on the next call).  Arguments as in
+ * mrrr_stein_batched; on return W and Z hold a valid solution.  The call
+ * synchronises the stream.  Device-side errors are returned.
+ */
+typedef struct mrrr_tuning {
+  int engine_blocks_per_sm;  /* chosen */
+  int configs;               /* candidates timed */
+  double width_scale;        /* chosen */
+  double best_ms;            /* time of the chosen candidate */
+  double default_ms;         /* time of the first candidate (the defaults) */
+} mrrr_tuning;
+
+mrrr_status mrrr_autotune_batched(mrrr_plan* plan, int batch, const int64_t* d_off, const double* d,
+                                  const double* e, const int* il, const int* iu, double* W,
+                                  const int64_t* w_off, double* Z, const int64_t* z_off, int64_t n_total,
+                                  int64_t k_total, int n_max, void* workspace, size_t ws_bytes,
+                                  mrrr_stream stream, mrrr_tuning* out);
 
 /*
  * mrrr_backward: gradient of a scalar loss L(W, Z) with respect to (d, e)

@@ -8,10 +8,10 @@ import importlib
 
 __all__ = ["Plan", "BatchLayout", "eigh_tridiagonal", "eigh_tridiagonal_batched", "build", "inputs",
            "EighTridiagonal", "eigh_tridiagonal_autograd", "EighTridiagonalBatched",
-           "eigh_tridiagonal_batched_autograd", "eigh_tridiagonal_backward"]
+           "eigh_tridiagonal_batched_autograd", "eigh_tridiagonal_backward", "autotune_batched"]
 
 _LAZY = {"Plan": "api", "BatchLayout": "api", "eigh_tridiagonal": "api", "eigh_tridiagonal_batched": "api",
-         "default_plan": "api", "eigh_tridiagonal_backward": "api", "EighTridiagonal": "autograd",
+         "default_plan": "api", "eigh_tridiagonal_backward": "api", "autotune_batched": "api", "EighTridiagonal": "autograd",
          "eigh_tridiagonal_autograd": "autograd", "EighTridiagonalBatched": "autograd",
          "eigh_tridiagonal_batched_autograd": "autograd"}
 

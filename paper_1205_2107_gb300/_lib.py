@@ -23,15 +23,16 @@ OK, ERR_ARG, ERR_WORKSPACE, ERR_NONFINITE, ERR_NOCONV, ERR_QUEUE, ERR_TIMEOUT, E
 EXPORTS = ["mrrr_options_default", "mrrr_plan_create", "mrrr_plan_destroy", "mrrr_workspace_size",
            "mrrr_stein", "mrrr_stein_batched", "mrrr_backward", "mrrr_backward_workspace_size",
            "mrrr_get_status", "mrrr_status_string", "mrrr_version", "mrrr_set_timing", "mrrr_get_profile",
-           "mrrr_eigenvalues_static"]
+           "mrrr_eigenvalues_static", "mrrr_autotune_batched"]
 STATIC_MAX_N = 8192  # MRRR_STATIC_MAX_N
 
 
 class Options(ctypes.Structure):
     _fields_ = [("gap_tol", c_double), ("classify_rtol", c_double), ("max_depth", c_int),
-                ("max_bisect_steps", c_int), ("reserved1", c_int), ("threads_per_block", c_int),
-                ("vec_blocks_per_sm", c_int), ("reserved0", c_int), ("max_nodes", c_int64),
-                ("pool_rows", c_int64), ("cluster_rtol", c_double), ("root_perturb", c_double)]
+                ("max_bisect_steps", c_int), ("engine_blocks_per_sm", c_int), ("threads_per_block", c_int),
+                ("vec_blocks_per_sm", c_int), ("use_graph", c_int), ("max_nodes", c_int64),
+                ("pool_rows", c_int64), ("cluster_rtol", c_double), ("root_perturb", c_double),
+                ("width_scale", c_double)]
 
 
 class Info(ctypes.Structure):
@@ -42,6 +43,11 @@ class Info(ctypes.Structure):
         out = {f: getattr(self, f) for f, _ in self._fields_ if f != "diag"}
         out["diag"] = list(self.diag)
         return out
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("engine_blocks_per_sm", c_int), ("configs", c_int), ("width_scale", c_double),
+                ("best_ms", c_double), ("default_ms", c_double)]
 
 
 class Profile(ctypes.Structure):
@@ -96,6 +102,8 @@ def load(build_if_missing: bool = False):
         lib.mrrr_set_timing.argtypes = [P, c_int]
         lib.mrrr_get_profile.argtypes = [P, ctypes.POINTER(Profile)]
         lib.mrrr_eigenvalues_static.argtypes = [c_int, dp, dp, c_int, c_int, dp, P]
+        lib.mrrr_autotune_batched.argtypes = [P, c_int, dp, dp, dp, dp, dp, dp, dp, dp, dp, c_int64, c_int64,
+                                              c_int, dp, c_size_t, P, ctypes.POINTER(Tuning)]
         for name in EXPORTS:
             if name not in ("mrrr_status_string", "mrrr_version"):
                 getattr(lib, name).restype = c_int

@@ -35,8 +35,11 @@ class Plan:
     """A solver plan (options + reusable device workspace) on one GPU.
 
     Options are the fields of ``mrrr_options`` (gap_tol, classify_rtol,
-    max_depth, max_bisect_steps, threads_per_block,
-    vec_blocks_per_sm, max_nodes, pool_rows); zero or absent means default.
+    max_depth, max_bisect_steps, engine_blocks_per_sm, threads_per_block,
+    vec_blocks_per_sm, use_graph, max_nodes, pool_rows, cluster_rtol,
+    root_perturb, width_scale); zero or absent means default.  With
+    ``use_graph=1`` a solve is captured once per call signature into a CUDA
+    graph and replayed.
     """
 
     def __init__(self, device: torch.device | int | None = None, **options):
@@ -304,3 +307,31 @@ def eigh_tridiagonal_backward(W: torch.Tensor, Z: torch.Tensor, Wbar: torch.Tens
     if check:
         torch.cuda.synchronize(dev)
     return dbar[:n_total], ebar[:n_total]
+
+
+def autotune_batched(d: torch.Tensor, e: torch.Tensor, layout: BatchLayout, *, plan: Plan | None = None,
+                     out=None) -> dict:
+    """Choose the batched solver's launch shape for this layout by timing
+    the candidates (mrrr_autotune_batched); the choice stays on the plan.
+
+    One checked solve runs first so that the plan's capacities fit the
+    batch.  Returns the chosen engine_blocks_per_sm and width_scale with the
+    best and default times (ms).
+    """
+    d = _check_input(d, "d")
+    e = _check_input(e, "e")
+    plan = plan or default_plan(d.device)
+    W, Z = eigh_tridiagonal_batched(d, e, layout, plan=plan, out=out)
+    call = _BatchedCall(plan, layout.batch, layout.offsets, d, e, layout.il, layout.iu, W, layout.w_offsets, Z,
+                        layout.z_offsets, layout.n_total, layout.k_total, layout.n_max)
+    nbytes = call.ws_bytes()
+    ws = plan.workspace(nbytes)
+    t = _lib.Tuning()
+    rc = _lib.load().mrrr_autotune_batched(
+        plan.handle, layout.batch, _ptr(layout.offsets), _ptr(d), _ptr(e), _ptr(layout.il), _ptr(layout.iu),
+        _ptr(W), _ptr(layout.w_offsets), _ptr(Z), _ptr(layout.z_offsets), layout.n_total, layout.k_total,
+        layout.n_max, _ptr(ws), nbytes, _stream_handle(d.device), ctypes.byref(t))
+    _lib.check(rc, "mrrr_autotune_batched")
+    plan.options.update(engine_blocks_per_sm=int(t.engine_blocks_per_sm), width_scale=float(t.width_scale))
+    return {"engine_blocks_per_sm": int(t.engine_blocks_per_sm), "width_scale": float(t.width_scale),
+            "best_ms": float(t.best_ms), "default_ms": float(t.default_ms), "configs": int(t.configs)}

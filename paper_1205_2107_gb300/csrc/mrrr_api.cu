@@ -9,6 +9,18 @@
 
 #include "mrrr_launch.h"
 
+// Everything a captured solve depends on: a replay is valid only for the
+// same arguments, workspace and options.
+struct GraphKey {
+  mrrr::ProblemArgs a;
+  const void *d, *e, *ws;
+  void *W, *Z;
+  int64_t n_total, k_total;
+  int n_max;
+  size_t ws_bytes;
+  int64_t opt_version;
+};
+
 struct mrrr_plan {
   mrrr_options opt;
   int device;
@@ -16,6 +28,13 @@ struct mrrr_plan {
   mrrr::Ctl* host_ctl;  // pinned, for the per-level count and the status
   void* last_ws;        // workspace of the last solve (for mrrr_get_status)
   mrrr::StageTimer timer;
+  int64_t opt_version;  // bumped when the autotuner changes the options
+  // CUDA graph of the last solve signature (use_graph)
+  cudaStream_t cap_stream;
+  cudaGraphExec_t exec;
+  GraphKey key;
+  bool have_graph;
+  int64_t graph_launches;
 };
 
 namespace mrrr {
@@ -182,6 +201,8 @@ Dev make_dev(const mrrr_plan* p, const Layout& L, void* ws, int batch, const dou
   v.root_perturb = o.root_perturb;
   v.max_depth = o.max_depth;
   v.max_bisect = o.max_bisect_steps;
+  v.engine_ctas = o.engine_blocks_per_sm;
+  v.width_scale = o.width_scale;
   return v;
 }
 
@@ -197,8 +218,13 @@ Grid make_grid(const mrrr_plan* p, int64_t max_slots) {
 
 mrrr_status cuda_status(cudaError_t e) { return e == cudaSuccess ? MRRR_OK : MRRR_ERR_CUDA; }
 
+// One solve enqueued on s.  device_levels: every level up to max_depth is
+// enqueued without host synchronisation and the level kernels return at
+// once after the tree is complete (used for graph capture); otherwise the
+// host reads the new-cluster count after each level and stops there.
 mrrr_status solve(mrrr_plan* p, const ProblemArgs& a, const double* d, const double* e, double* W, double* Z,
-                  int64_t n_total, int64_t k_total, int n_max, void* ws, size_t ws_bytes, cudaStream_t s) {
+                  int64_t n_total, int64_t k_total, int n_max, void* ws, size_t ws_bytes, cudaStream_t s,
+                  bool device_levels = false) {
   Layout L = make_layout(p, a.batch, n_total, k_total, n_max);
   if (!ws || ws_bytes < L.total) return MRRR_ERR_WORKSPACE;
   Dev v = make_dev(p, L, ws, a.batch, d, e, W, Z);
@@ -208,12 +234,20 @@ mrrr_status solve(mrrr_plan* p, const ProblemArgs& a, const double* d, const dou
   // Clusters from an earlier solve on this workspace must not leak into this
   // one: the per-slot arrays are fully rewritten by the setup kernels.
   StageTimer* tm = &p->timer;
-  if (std::getenv("MRRR_TIMING")) tm->on = true;
+  const bool timing_was = tm->on;
+  if (std::getenv("MRRR_TIMING") && !device_levels) tm->on = true;
+  if (device_levels) tm->on = false;  // no event records inside a capture
   set_stage_timer(tm);
   tm->begin(s);
   launch_setup(v, a, n_total, g, s);
+  if (device_levels) {
+    for (int level = 0; level <= p->opt.max_depth; ++level) {
+      launch_level_classify(v, level, g, s);
+      launch_level_children(v, level, g, s);
+    }
+  }
   int levels = 0;
-  for (int level = 0; level <= p->opt.max_depth; ++level) {
+  for (int level = 0; !device_levels && level <= p->opt.max_depth; ++level) {
     launch_level_classify(v, level, g, s);
     tm->mark("classify", s);
     if (cudaMemcpyAsync(p->host_ctl, v.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -232,9 +266,60 @@ mrrr_status solve(mrrr_plan* p, const ProblemArgs& a, const double* d, const dou
   tm->mark("vectors", s);
   tm->finish();
   set_stage_timer(nullptr);
-  // record the number of levels in the device control block
+  tm->on = timing_was;
   (void)levels;
   return cuda_status(cudaGetLastError());
+}
+
+// use_graph: capture the device-driven solve once per call signature on the
+// plan's own stream, then replay the graph on the caller's stream.
+mrrr_status solve_graph(mrrr_plan* p, const ProblemArgs& a, const double* d, const double* e, double* W, double* Z,
+                        int64_t n_total, int64_t k_total, int n_max, void* ws, size_t ws_bytes, cudaStream_t s) {
+  if (!ws || ws_bytes < make_layout(p, a.batch, n_total, k_total, n_max).total) return MRRR_ERR_WORKSPACE;
+  GraphKey k{};
+  k.a = a;
+  k.d = d;
+  k.e = e;
+  k.ws = ws;
+  k.W = W;
+  k.Z = Z;
+  k.n_total = n_total;
+  k.k_total = k_total;
+  k.n_max = n_max;
+  k.ws_bytes = ws_bytes;
+  k.opt_version = p->opt_version;
+  if (!p->have_graph || std::memcmp(&k, &p->key, sizeof(k)) != 0) {
+    if (p->have_graph) {
+      cudaGraphExecDestroy(p->exec);
+      p->have_graph = false;
+    }
+    if (!p->cap_stream && cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+      return MRRR_ERR_CUDA;
+    if (cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return MRRR_ERR_CUDA;
+    const mrrr_status st = solve(p, a, d, e, W, Z, n_total, k_total, n_max, ws, ws_bytes, p->cap_stream, true);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(p->cap_stream, &graph);
+    if (st != MRRR_OK || ce != cudaSuccess || !graph) {
+      if (graph) cudaGraphDestroy(graph);
+      return st != MRRR_OK ? st : MRRR_ERR_CUDA;
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&p->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) return MRRR_ERR_CUDA;
+    std::memcpy(&p->key, &k, sizeof(k));
+    p->have_graph = true;
+    p->graph_launches = p->timer.launches;
+  }
+  p->last_ws = ws;
+  p->timer.launches = p->graph_launches;
+  p->timer.nstages = 0;
+  return cuda_status(cudaGraphLaunch(p->exec, s));
+}
+
+mrrr_status dispatch(mrrr_plan* p, const ProblemArgs& a, const double* d, const double* e, double* W, double* Z,
+                     int64_t n_total, int64_t k_total, int n_max, void* ws, size_t ws_bytes, cudaStream_t s) {
+  if (p->opt.use_graph) return solve_graph(p, a, d, e, W, Z, n_total, k_total, n_max, ws, ws_bytes, s);
+  return solve(p, a, d, e, W, Z, n_total, k_total, n_max, ws, ws_bytes, s);
 }
 
 }  // namespace
@@ -255,6 +340,8 @@ mrrr_status mrrr_options_default(mrrr_options* opt) {
   opt->vec_blocks_per_sm = 8;
   opt->cluster_rtol = 0x1p-40;
   opt->root_perturb = 64.0;
+  opt->engine_blocks_per_sm = 2;
+  opt->width_scale = 1.0;
   return MRRR_OK;
 }
 
@@ -275,6 +362,9 @@ mrrr_status mrrr_plan_create(mrrr_plan** plan, const mrrr_options* opt) {
     if (opt->cluster_rtol > 0) o.cluster_rtol = opt->cluster_rtol;
     if (opt->root_perturb > 0) o.root_perturb = opt->root_perturb;
     if (opt->root_perturb < 0) o.root_perturb = 0.0;  // negative: no perturbation
+    if (opt->use_graph > 0) o.use_graph = 1;
+    if (opt->engine_blocks_per_sm > 0) o.engine_blocks_per_sm = std::min(opt->engine_blocks_per_sm, 2);
+    if (opt->width_scale > 0) o.width_scale = opt->width_scale;
   }
   if (o.gap_tol >= 1.0 || o.classify_rtol >= 0.25 || o.threads_per_block % 32 != 0) return MRRR_ERR_ARG;
   int dev = 0, nsm = 0;
@@ -286,6 +376,11 @@ mrrr_status mrrr_plan_create(mrrr_plan** plan, const mrrr_options* opt) {
   p->device = dev;
   p->nsm = nsm;
   p->last_ws = nullptr;
+  p->opt_version = 0;
+  p->cap_stream = nullptr;
+  p->exec = nullptr;
+  p->have_graph = false;
+  p->graph_launches = 0;
   if (cudaMallocHost(&p->host_ctl, sizeof(Ctl)) != cudaSuccess) {
     delete p;
     return MRRR_ERR_CUDA;
@@ -297,6 +392,8 @@ mrrr_status mrrr_plan_create(mrrr_plan** plan, const mrrr_options* opt) {
 
 mrrr_status mrrr_plan_destroy(mrrr_plan* plan) {
   if (!plan) return MRRR_ERR_ARG;
+  if (plan->have_graph) cudaGraphExecDestroy(plan->exec);
+  if (plan->cap_stream) cudaStreamDestroy(plan->cap_stream);
   cudaFreeHost(plan->host_ctl);
   delete plan;
   return MRRR_OK;
@@ -322,8 +419,8 @@ mrrr_status mrrr_stein(mrrr_plan* plan, int n, const double* d, const double* e,
   a.ldz = Z ? ldz : n;
   // a 1x1 problem has no off-diagonal; any non-null pointer is never read
   const double* ee = (n > 1) ? e : d;
-  return solve(plan, a, d, ee, W, Z, n, (int64_t)(iu - il + 1), n, workspace, ws_bytes,
-               static_cast<cudaStream_t>(stream));
+  return dispatch(plan, a, d, ee, W, Z, n, (int64_t)(iu - il + 1), n, workspace, ws_bytes,
+                  static_cast<cudaStream_t>(stream));
 }
 
 mrrr_status mrrr_stein_batched(mrrr_plan* plan, int batch, const int64_t* d_off, const double* d, const double* e,
@@ -340,8 +437,73 @@ mrrr_status mrrr_stein_batched(mrrr_plan* plan, int batch, const int64_t* d_off,
   a.iu = iu;
   a.w_off = w_off;
   a.z_off = z_off;
-  return solve(plan, a, d, e, W, Z, n_total, k_total, n_max, workspace, ws_bytes,
-               static_cast<cudaStream_t>(stream));
+  return dispatch(plan, a, d, e, W, Z, n_total, k_total, n_max, workspace, ws_bytes,
+                  static_cast<cudaStream_t>(stream));
+}
+
+mrrr_status mrrr_autotune_batched(mrrr_plan* plan, int batch, const int64_t* d_off, const double* d,
+                                  const double* e, const int* il, const int* iu, double* W, const int64_t* w_off,
+                                  double* Z, const int64_t* z_off, int64_t n_total, int64_t k_total, int n_max,
+                                  void* workspace, size_t ws_bytes, mrrr_stream stream, mrrr_tuning* out) {
+  if (!plan || !out || batch <= 0 || n_total <= 0 || k_total < 0 || n_max <= 0) return MRRR_ERR_ARG;
+  if (!d_off || !d || !e || !W || !w_off || (Z && !z_off)) return MRRR_ERR_ARG;
+  ProblemArgs a{};
+  a.batch = batch;
+  a.d_off = d_off;
+  a.il = il;
+  a.iu = iu;
+  a.w_off = w_off;
+  a.z_off = z_off;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  static const int kCtas[] = {2, 1};
+  static const double kWidth[] = {1.0, 0.5, 2.0};
+  const mrrr_options saved = plan->opt;
+  const bool timing = plan->timer.on;
+  plan->timer.on = false;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return MRRR_ERR_CUDA;
+  std::memset(out, 0, sizeof(*out));
+  double best = INFINITY;
+  mrrr_status st = MRRR_OK;
+  int tried = 0;
+  // one untimed solve first: the timed candidates then all run warm
+  plan->opt.use_graph = 0;
+  st = solve(plan, a, d, e, W, Z, n_total, k_total, n_max, workspace, ws_bytes, s, true);
+  for (int ci = 0; ci < 2 && st == MRRR_OK; ++ci) {
+    for (int wi = 0; wi < 3 && st == MRRR_OK; ++wi) {
+      plan->opt.engine_blocks_per_sm = kCtas[ci];
+      plan->opt.width_scale = kWidth[wi];
+      cudaEventRecord(e0, s);
+      st = solve(plan, a, d, e, W, Z, n_total, k_total, n_max, workspace, ws_bytes, s, true);
+      cudaEventRecord(e1, s);
+      if (st != MRRR_OK || cudaEventSynchronize(e1) != cudaSuccess) break;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      const mrrr_status dev = mrrr_get_status(plan, stream, nullptr);
+      if (dev != MRRR_OK && dev != MRRR_ERR_NOCONV) {
+        st = dev;
+        break;
+      }
+      if (tried == 0) out->default_ms = ms;
+      ++tried;
+      if (ms < best) {
+        best = ms;
+        out->engine_blocks_per_sm = kCtas[ci];
+        out->width_scale = kWidth[wi];
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  plan->opt = saved;
+  plan->timer.on = timing;
+  if (st != MRRR_OK) return st;
+  plan->opt.engine_blocks_per_sm = out->engine_blocks_per_sm;
+  plan->opt.width_scale = out->width_scale;
+  ++plan->opt_version;
+  out->best_ms = best;
+  out->configs = tried;
+  return MRRR_OK;
 }
 
 mrrr_status mrrr_get_status(mrrr_plan* plan, mrrr_stream stream, mrrr_info* out) {

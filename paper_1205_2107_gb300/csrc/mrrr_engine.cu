@@ -101,6 +101,7 @@ __device__ __forceinline__ bool slot_is_long(const Dev& v, int64_t w) {
 // long intervals from the front (nlist), short ones from the back (nlist2).
 template <int MODE>
 __global__ void k_list(Dev v) {
+  if ((MODE == MODE_PREREFINE || MODE == MODE_REFINE) && v.ctl->done) return;
   const int lane = threadIdx.x & 31;
   const int64_t nslots = v.ctl->nslots;
   const int level_begin = v.ctl->level_begin;
@@ -285,7 +286,7 @@ __global__ void __launch_bounds__(kEngThreads, kEngCtasPerSm) k_engine(Dev v) {
   const int lane = threadIdx.x & 31;
   const long long nlong = min(v.ctl->nlist, (long long)v.max_list);
   const long long nshort = min(v.ctl->nlist2, (long long)v.max_list - nlong);
-  const long long lanes_total = (long long)gridDim.x * blockDim.x;
+  const long long lanes_total = (long long)((double)gridDim.x * blockDim.x * v.width_scale);
   const double rtol = mode_rtol<MODE>(v);
   const int maxsteps = v.max_bisect;
   for (int phase = 0; phase < 2; ++phase) {
@@ -354,7 +355,7 @@ void launch_engine_mode(const Dev& v, const Grid& g, cudaStream_t s) {
   count_launch();
   k_list<MODE><<<g.slot_blocks, 128, 0, s>>>(v);
   count_launch();
-  k_engine<MODE><<<g.nsm * kEngCtasPerSm, kEngThreads, 0, s>>>(v);
+  k_engine<MODE><<<g.nsm * max(1, min(kEngCtasPerSm, v.engine_ctas)), kEngThreads, 0, s>>>(v);
   count_launch();
 }
 

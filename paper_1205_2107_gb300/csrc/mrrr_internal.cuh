@@ -98,6 +98,8 @@ struct Ctl {
   long long list_next;    // next long entry to hand out
   long long nlist2;       // short intervals (back of the list)
   long long list_next2;   // next short entry to hand out
+  int done;               // the tree is complete: later levels' kernels exit at once
+  int pad4_;
 };
 
 // Indices of Ctl::diag (mirrored in mrrr_info.diag).
@@ -160,6 +162,8 @@ struct Dev {
   double root_perturb;  // root perturbation size in ulps
   int max_depth;
   int max_bisect;
+  int engine_ctas;      // engine CTAs per SM (1 or 2)
+  double width_scale;   // multiplies the resident lanes when choosing the multisection width
 };
 
 __device__ __forceinline__ void set_status(Ctl* c, int code) {

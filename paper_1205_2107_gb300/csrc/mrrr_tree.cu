@@ -14,9 +14,21 @@ namespace mrrr {
 namespace {
 
 __global__ void k_level_start(Dev v) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
+  if (threadIdx.x == 0 && blockIdx.x == 0 && !v.ctl->done) {
     v.ctl->level_begin = v.ctl->nodes;
     v.ctl->level_new = 0;
+  }
+}
+
+// After a level's classification: the tree is complete when the level made
+// no new cluster (or a fatal error was recorded); the kernels of all later
+// levels then return at entry, so the levels can be enqueued without the
+// host reading the count in between.
+__global__ void k_level_end(Dev v, int level) {
+  if (threadIdx.x == 0 && blockIdx.x == 0 && !v.ctl->done) {
+    v.ctl->levels = level + 1;
+    const int st = v.ctl->status;
+    if (v.ctl->level_new == 0 || (st != 0 && st != MRRR_ERR_NOCONV)) v.ctl->done = 1;
   }
 }
 
@@ -30,6 +42,7 @@ __global__ void k_level_start(Dev v) {
 constexpr double kSmallBlockTol = 1.0;
 
 __global__ void k_classify_flags(Dev v, int level) {
+  if (v.ctl->done) return;
   const int64_t nslots = v.ctl->nslots;
   for (int64_t w = gtid(); w < nslots; w += gstride()) {
     if (v.state[w] != SLOT_ACTIVE) continue;
@@ -49,6 +62,7 @@ __global__ void k_classify_flags(Dev v, int level) {
 
 // Runs between boundaries: length 1 = singleton, otherwise a new child node.
 __global__ void k_classify_runs(Dev v, int level) {
+  if (v.ctl->done) return;
   const int64_t nslots = v.ctl->nslots;
   for (int64_t w = gtid(); w < nslots; w += gstride()) {
     if (v.state[w] != SLOT_ACTIVE) continue;
@@ -175,6 +189,7 @@ __device__ __forceinline__ void set_child(Dev& v, int64_t id, Node c, const Node
 // is at most 8 spdiam; otherwise the node is marked for phase 2.  Nodes
 // whose rows do not fit take the fallback (their vectors at the parent).
 __global__ void k_childrep_first(Dev v) {
+  if (v.ctl->done) return;
   const int begin = v.ctl->level_begin;
   const int end = min(v.ctl->nodes, v.max_nodes);
   for (int64_t id = begin + gtid(); id < end; id += gstride()) {
@@ -227,6 +242,7 @@ constexpr int kPhase2Group = 8;
 __constant__ int kPhase2Cands[kPhase2Group] = {1, 2, 3, 4, 8, 9, 18, 19};
 
 __global__ void k_childrep(Dev v) {
+  if (v.ctl->done) return;
   const int lane = threadIdx.x & 31;
   const int sub = lane / kPhase2Group, gl = lane % kPhase2Group, leader = sub * kPhase2Group;
   const int per_warp = 32 / kPhase2Group;
@@ -287,6 +303,8 @@ void launch_level_classify(const Dev& v, int level, const Grid& g, cudaStream_t 
   k_classify_flags<<<g.slot_blocks, g.tpb, 0, s>>>(v, level);
   count_launch();
   k_classify_runs<<<g.slot_blocks, g.tpb, 0, s>>>(v, level);
+  count_launch();
+  k_level_end<<<1, 32, 0, s>>>(v, level);
   count_launch();
 }
 
