@@ -374,9 +374,29 @@ def side_by_side(args, dev, flush):
     def batched():
         api.eigh_tridiagonal_batched(dt, et, lay, plan=plan, check=False, out=(W, Z))
 
+    # a checked solve first: it grows the plan's node table and representation
+    # pool to what this batch needs (an unchecked solve that overflowed would
+    # take the capacity fallback and time the wrong work)
+    api.eigh_tridiagonal_batched(dt, et, lay, plan=plan, out=(W, Z))
     batched()
     torch.cuda.synchronize()
-    t_b = _time_cuda(batched, 2, flush)
+    t_direct = _time_cuda(batched, 2, flush)
+    if plan.info()["status"] != 0:
+        raise SystemExit("batched solve reported an error")
+    # autotuned launch shape, then the solve captured into a CUDA graph and replayed
+    tune = api.autotune_batched(dt, et, lay, plan=plan, out=(W, Z))
+    gplan = api.Plan(dev, use_graph=1, engine_blocks_per_sm=tune["engine_blocks_per_sm"],
+                     width_scale=tune["width_scale"], pool_rows=plan.options.get("pool_rows", 0),
+                     max_nodes=plan.options.get("max_nodes", 0))
+
+    def replay():
+        api.eigh_tridiagonal_batched(dt, et, lay, plan=gplan, check=False, out=(W, Z))
+
+    t_first = _time_cuda(replay, 1, flush)  # capture + instantiate + first replay
+    if gplan.info()["status"] != 0:
+        raise SystemExit("batched graph solve reported an error")
+    t_b = _time_cuda(replay, 2, flush)
+    launches_b = gplan.profile()["launches"]
     nk_b = sum(n * n for n in sizes)
     # plain solver looped over every 16th problem (same sizes mix), scaled to the batch
     sample = list(range(0, len(sizes), 16))
@@ -393,6 +413,9 @@ def side_by_side(args, dev, flush):
         "workload": "4096 STEPs, n log-uniform in [32, 2048] (seed 2107), d, e iid U[-1,1], all eigenpairs",
         "ms": t_b, "eigenpairs_per_s": sum(sizes) / (t_b * 1e-3), "matrices_per_s": len(sizes) / (t_b * 1e-3),
         "path_roofline_frac": 1e3 * PATH_FLOPS_PER_ROW * nk_b / (FP64_PEAK_GFLOPS * 1e9) / t_b,
+        "timing": "CUDA graph replay (levels driven on the device), autotuned launch shape",
+        "graph_launches": launches_b, "first_call_ms": t_first, "direct_launch_ms": t_direct,
+        "autotune": tune,
         "plain_loop": {"problems": len(sample), "ms": t_p, "eigenpairs_per_s": n_sample / (t_p * 1e-3),
                        "matrices_per_s": len(sample) / (t_p * 1e-3)},
     }

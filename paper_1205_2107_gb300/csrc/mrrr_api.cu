@@ -123,7 +123,7 @@ Layout make_layout(const mrrr_plan* p, int batch, int64_t n_total, int64_t k_tot
     // automatic: room for many full-size child representations; a solve that
     // needs more reports MRRR_ERR_QUEUE and the needed rows in mrrr_info
     int64_t want = (std::max<int64_t>(k_total, 1) + 1) * std::max<int64_t>(n_max, 1);
-    int64_t cap = std::max<int64_t>(32 * n_total, (int64_t)1 << 28);
+    int64_t cap = std::max<int64_t>(256 * n_total, (int64_t)1 << 28);
     pool_child = std::min(want, cap);
   }
   L.pool_rows = n_total + pool_child;
