@@ -198,6 +198,27 @@ def run_reference(args, rank: int, world: int):
 
 
 # ---------------------------------------------------------------------------
+# multi-rank aggregation (replicas: every rank solves the same workload)
+
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest value of x over all ranks (the job takes as long as its
+    slowest rank); x itself when running alone."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank_step: int, steps: int, total_ms: float, world: int) -> float:
+    """Units per second for the whole job: every rank processed
+    units_per_rank_step units per step, in total_ms (max over ranks)."""
+    return world * units_per_rank_step * steps / (total_ms * 1e-3)
+
+
+# ---------------------------------------------------------------------------
 # GPU leg
 
 def run_ours(args, rank: int, world: int):
@@ -258,12 +279,8 @@ def run_ours(args, rank: int, world: int):
         if info["status"] != 0:
             raise SystemExit(f"solver reported status {info['status']} ({info})")
         plan.set_timing(False)
-    total_ms = sum(times)
-    tmax = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-    total_ms = float(tmax.item())
-    value = world * pairs_per_step * args.steps / (total_ms * 1e-3)
+    total_ms = max_over_ranks(sum(times), world, dev)
+    value = whole_job_rate(pairs_per_step, args.steps, total_ms, world)
 
     # end to end through the public API with host buffers: d, e copied in
     # from pinned memory, W and Z copied back into pinned memory, every step
@@ -291,7 +308,7 @@ def run_ours(args, rank: int, world: int):
         t0 = time.perf_counter()
         e2e_step(check=False)
         e2e_times.append(time.perf_counter() - t0)
-    e2e_value = world * pairs_per_step * args.steps / sum(e2e_times)
+    e2e_value = whole_job_rate(pairs_per_step, args.steps, max_over_ranks(1e3 * sum(e2e_times), world, dev), world)
     del hostout
 
     # roofline of the dominant kernel: the persistent interval engine (every
