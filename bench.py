@@ -231,18 +231,21 @@ def run_ours(args, rank: int, world: int):
     dev = torch.device("cuda", local)
     build.build()
     mats = workload_matrices()
-    dmats = [(nm, torch.tensor(d, device=dev), torch.tensor(np.append(e, 0.0), device=dev))
-             for nm, d, e in mats]
-    pairs_per_step = sum(len(d) for _, d, _ in mats)
-    plans = [api.Plan(local) for _ in mats]
+    sizes = [len(d) for _, d, _ in mats]
+    pairs_per_step = sum(sizes)
+    # both matrices in one batched solve: their cluster levels share launches
+    lay = api.BatchLayout(sizes, dev)
+    d_cat = torch.tensor(np.concatenate([d for _, d, _ in mats]), device=dev)
+    e_cat = torch.tensor(np.concatenate([np.append(e, 0.0) for _, _, e in mats]), device=dev)
+    plan = api.Plan(local)
+    plans = [plan]
+    W_out = torch.empty(lay.k_total, dtype=torch.float64, device=dev)
+    Z_out = torch.empty(lay.z_total, dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
     def step(check: bool):
-        out = []
-        for (nm, d, e), plan in zip(dmats, plans):
-            out.append(api.eigh_tridiagonal(d, e, plan=plan, check=check))
-        return out
+        return api.eigh_tridiagonal_batched(d_cat, e_cat, lay, plan=plan, check=check, out=(W_out, Z_out))
 
     def barrier():
         if world > 1:
@@ -282,20 +285,34 @@ def run_ours(args, rank: int, world: int):
     total_ms = max_over_ranks(sum(times), world, dev)
     value = whole_job_rate(pairs_per_step, args.steps, total_ms, world)
 
+    # the same two matrices solved one after the other by the single-problem
+    # path (for comparison only)
+    seq_plans = [api.Plan(local) for _ in mats]
+    dmats = [(torch.tensor(d, device=dev), torch.tensor(np.append(e, 0.0), device=dev)) for _, d, e in mats]
+
+    def sequential():
+        for (d, e), pl in zip(dmats, seq_plans):
+            api.eigh_tridiagonal(d, e, plan=pl, check=False)
+
+    for (d, e), pl in zip(dmats, seq_plans):
+        api.eigh_tridiagonal(d, e, plan=pl)
+    t_seq = _time_cuda(sequential, 2, flush)
+    del dmats, seq_plans
+
     # end to end through the public API with host buffers: d, e copied in
     # from pinned memory, W and Z copied back into pinned memory, every step
-    hostd = [(torch.tensor(d).pin_memory(), torch.tensor(np.append(e, 0.0)).pin_memory()) for _, d, e in mats]
-    hostout = [(torch.empty(len(d), dtype=torch.float64, pin_memory=True),
-                torch.empty((len(d), len(d)), dtype=torch.float64, pin_memory=True)) for _, d, _ in mats]
-    h2d = sum(a.numel() * 8 + b.numel() * 8 for a, b in hostd)
-    d2h = sum(w.numel() * 8 + z.numel() * 8 for w, z in hostout)
+    hd = d_cat.cpu().pin_memory()
+    he = e_cat.cpu().pin_memory()
+    hw = torch.empty(lay.k_total, dtype=torch.float64, pin_memory=True)
+    hz = torch.empty(lay.z_total, dtype=torch.float64, pin_memory=True)
+    h2d = (hd.numel() + he.numel()) * 8
+    d2h = (hw.numel() + hz.numel()) * 8
 
     def e2e_step(check: bool):
-        for (hd, he), (hw, hz), plan in zip(hostd, hostout, plans):
-            W, Z = api.eigh_tridiagonal(hd.to(dev, non_blocking=True), he.to(dev, non_blocking=True), plan=plan,
-                                        check=check)
-            hw.copy_(W, non_blocking=True)
-            hz.copy_(Z.t(), non_blocking=True)  # Z is column-major: its transpose is contiguous
+        W, Z = api.eigh_tridiagonal_batched(hd.to(dev, non_blocking=True), he.to(dev, non_blocking=True), lay,
+                                            plan=plan, check=check, out=(W_out, Z_out))
+        hw.copy_(W[:lay.k_total], non_blocking=True)
+        hz.copy_(Z[:lay.z_total], non_blocking=True)
         torch.cuda.synchronize(dev)
 
     for _ in range(2):
@@ -309,7 +326,7 @@ def run_ours(args, rank: int, world: int):
         e2e_step(check=False)
         e2e_times.append(time.perf_counter() - t0)
     e2e_value = whole_job_rate(pairs_per_step, args.steps, max_over_ranks(1e3 * sum(e2e_times), world, dev), world)
-    del hostout
+    del hz
 
     # roofline of the dominant kernel: the persistent interval engine (every
     # bisection stage), against the bisection part of the fixed flop model
@@ -344,8 +361,9 @@ def run_ours(args, rank: int, world: int):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": [len(d) for _, d, _ in mats],
-                       "eigenpairs_per_step": pairs_per_step,
+            "config": {"workload": WORKLOAD, "n": sizes, "eigenpairs_per_step": pairs_per_step,
+                       "schedule": "both matrices in one batched solve (mrrr_stein_batched)",
+                       "sequential_plain_ms": t_seq,
                        "l2": "flushed before each step (256 MB write); Z output 3.2 GB per matrix",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "clocks": clocks, "gpu_launches": launches,
