@@ -179,3 +179,30 @@ def test_tiny_pool_grows_and_succeeds():
     d, e = inputs.wilkinson_plus(301)
     assert_parity(d, e, plan=plan)
     assert plan.options["pool_rows"] > 1
+
+
+@pytest.mark.parametrize("scale_exp", [-900, -300, 300, 900])
+def test_extreme_scaling_is_exact(scale_exp):
+    """Power-of-two scalings of T by 2^k scale W by exactly 2^k (the solver
+    scales G(T) into [1, 2) internally) and leave Z unchanged."""
+    d, e = inputs.uniform(300, 77)
+    W0, Z0 = solve(d, e)
+    f = 2.0 ** scale_exp
+    W1, Z1 = solve(d * f, e * f)
+    assert torch.equal(W1, W0 * f)
+    assert torch.equal(Z1, Z0)
+
+
+def test_graded_matrix():
+    """Entries graded over many orders of magnitude (d_i = 10^(-i/10),
+    e_i = sqrt(d_i d_{i+1}) / 2): parity with the oracle."""
+    n = 150
+    d = 10.0 ** (-np.arange(n) / 10.0)
+    e = 0.5 * np.sqrt(d[:-1] * d[1:])
+    assert_parity(d, e)
+
+
+def test_two_by_two_subsets():
+    d, e = np.array([1.0, 3.0]), np.array([2.0])
+    for il, iu in [(1, 1), (2, 2), (1, 2)]:
+        assert_parity(d, e, il, iu)
