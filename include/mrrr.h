@@ -58,8 +58,9 @@ typedef enum mrrr_status {
 /* Tunables.  Zero-initialise and call mrrr_options_default(); fields left at
    0 keep their defaults. */
 typedef struct mrrr_options {
-  double gap_tol;          /* singleton threshold on the relative gap (1e-3, Sec. 3.1.1);
-                              a block of order m < 1000 uses max(gap_tol, 1/m) */
+  double gap_tol;          /* floor of the singleton threshold on the relative gap:
+                              a block of order m uses tol = max(gap_tol, 1/m)
+                              (default 1e-4; 1e-3 is the paper's value, Sec. 3.1.1) */
   double classify_rtol;    /* relative interval width reached by bisection before
                               classification (2^-20) */
   int max_depth;           /* cluster-tree depth limit (64); deeper clusters take the

@@ -332,7 +332,7 @@ extern "C" {
 mrrr_status mrrr_options_default(mrrr_options* opt) {
   if (!opt) return MRRR_ERR_ARG;
   std::memset(opt, 0, sizeof(*opt));
-  opt->gap_tol = 1e-3;
+  opt->gap_tol = 1e-4;
   opt->classify_rtol = 0x1p-20;
   opt->max_depth = 64;
   opt->max_bisect_steps = 256;

@@ -35,10 +35,11 @@ __global__ void k_level_end(Dev v, int level) {
 // Boundary flags: a cluster ends after slot w when the (lower bound of the)
 // absolute gap to w+1 is at least tol times the larger magnitude of the two.
 // tol = max(gap_tol, 1 / m) for a block of order m.  Eq. errorangle bounds
-// the error angle of a singleton's vector by O(m eps / relgap); on random
-// matrices it behaves like c eps / relgap with c of a few units whatever m
-// is, while the orthogonality goal is 20 m eps, so for small blocks relgap
-// has to exceed about 1/m (below m = 1000 the threshold rises above 1e-3).
+// the error angle of a singleton's vector by O(m eps / relgap); measured, it
+// behaves like c eps / relgap with c of a few units whatever m is, while the
+// orthogonality goal is 20 m eps.  So relgap has to exceed about 1/m for
+// small blocks, and large blocks can accept smaller gaps than the paper's
+// 1e-3 (fewer, shallower cluster levels): the floor gap_tol defaults to 1e-4.
 constexpr double kSmallBlockTol = 1.0;
 
 __global__ void k_classify_flags(Dev v, int level) {

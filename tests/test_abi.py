@@ -41,7 +41,7 @@ def test_built_for_sm103a_only():
 def test_options_defaults(lib):
     o = _lib.Options()
     assert lib.mrrr_options_default(ctypes.byref(o)) == 0
-    assert o.gap_tol == 1e-3
+    assert o.gap_tol == 1e-4  # floor; blocks of order m use max(gap_tol, 1/m)
     assert o.classify_rtol == 2.0 ** -20
     assert o.max_depth == 64 and o.threads_per_block % 32 == 0
     assert lib.mrrr_options_default(None) == _lib.ERR_ARG
