@@ -153,7 +153,9 @@ Layout make_layout(const mrrr_plan* p, int batch, int64_t n_total, int64_t k_tot
   L.spos = take(sizeof(int) * (size_t)L.max_slots);
   L.state = take(sizeof(int) * (size_t)L.max_slots);
   L.bflag = take((size_t)L.max_slots);
-  L.vscr = take(sizeof(double) * (size_t)L.vscr_threads * (size_t)L.vscr_rows);
+  // the vector scratch also holds the FP32 copy of the root rows (one
+  // float2 per row) during root bisection
+  L.vscr = take(sizeof(double) * std::max<size_t>((size_t)L.vscr_threads * (size_t)L.vscr_rows, (size_t)n_total));
   L.total = off;
   return L;
 }

@@ -128,6 +128,85 @@ __global__ void k_list(Dev v) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// FP32 pre-bisection of the root intervals.  A root representation is
+// definite (T - sigma I with sigma outside the spectrum), so rounding its
+// entries to FP32 (relative perturbation 2^-24 each) moves every eigenvalue
+// by a small relative amount.  The FP32 pipe issues about 60 times faster
+// than the FP64 pipe on this part, so the first halvings of every root
+// interval run on an FP32 copy of the rows, down to a relative width of
+// kRoot32Width.  FP64 then confirms the bracket, widened by kRoot32Margin
+// relative and grown until two FP64 counts hold it, before bisecting to the
+// classification accuracy.  No FP32 result is trusted without that check.
+constexpr float kRoot32Width = 0x1p-13f;
+constexpr double kRoot32Margin = 0x1p-11;
+constexpr float kPivmin32 = 0x1p-60f;
+
+// FP32 rows of the root representations (D, LLD), in the eigenvector
+// scratch, which is unused until the vectors are computed.
+__device__ __forceinline__ float2* root32_rows(const Dev& v) { return reinterpret_cast<float2*>(v.vscr); }
+
+__global__ void k_root32_copy(Dev v, int64_t n_total) {
+  float2* r = root32_rows(v);
+  for (int64_t i = gtid(); i < n_total; i += gstride()) {
+    const double2 x = v.rep_dl[i];  // root representations occupy the first n_total pool rows
+    r[i] = make_float2((float)x.x, (float)x.y);
+  }
+}
+
+// The division-free Sturm count of count_step() in FP32.
+__device__ __forceinline__ int negcount32(const float2* __restrict__ r, int m, float tau) {
+  const int pivexp = (__float_as_int(kPivmin32) >> 23) & 0xff;
+  float a = -tau, b = 1.0f;
+  int neg = 0;
+  for (int i = 0; i < m; ++i) {
+    const float2 x = r[i];
+    float c = fmaf(x.x, b, a);
+    int ci = __float_as_int(c);
+    const int bi = __float_as_int(b);
+    int cexp = (ci >> 23) & 0xff;
+    if (cexp < pivexp) {
+      c = bi < 0 ? kPivmin32 : -kPivmin32;
+      ci = __float_as_int(c);
+      cexp = pivexp;
+    }
+    neg += (ci ^ bi) < 0;
+    const float an = fmaf(x.y, a, -tau * c);
+    const int k = cexp - 127;
+    b = __int_as_float((ci & 0x807fffff) | 0x3f800000);
+    const int ai = __float_as_int(an);
+    const int aexp = (ai >> 23) & 0xff;
+    a = (aexp - k <= 0) ? 0.0f : (aexp - k >= 255 ? __int_as_float((ai & 0x80000000) | 0x7f000000)
+                                                   : __int_as_float(ai - (k << 23)));
+  }
+  return neg;
+}
+
+// One thread per root interval of the list: FP32 bisection from the block's
+// Gershgorin bracket; the result goes to lo/hi for the FP64 check.
+__global__ void k_root32(Dev v) {
+  const long long nlist = min(v.ctl->nlist, (long long)v.max_list);
+  const float2* rows = root32_rows(v);
+  for (long long it = gtid(); it < nlist; it += gstride()) {
+    const int64_t w = v.ilist[it];
+    const Node nd = v.node[v.snode[w]];
+    const Block bk = v.blk[nd.block];
+    const int j = v.sj[w];
+    float lo = (float)bk.gl, hi = (float)bk.gu;
+    for (int step = 0; step < 48; ++step) {
+      if (hi - lo <= kRoot32Width * fmaxf(fabsf(lo), fabsf(hi))) break;
+      const float mid = 0.5f * (lo + hi);
+      if (!(mid > lo && mid < hi)) break;
+      if (negcount32(rows + bk.row0, bk.m, mid) >= j)
+        hi = mid;
+      else
+        lo = mid;
+    }
+    v.lo[w] = (double)lo;
+    v.hi[w] = (double)hi;
+  }
+}
+
 // Per-interval state, replicated in every lane of the interval's group.
 struct Iv {
   double lo, hi, plo, phi, delta, atol, pivmin;
@@ -152,8 +231,14 @@ __device__ __forceinline__ void iv_load(const Dev& v, int64_t w, Iv& q) {
   q.tries = 0;
   q.phase = PH_BISECT;
   if (MODE == MODE_ROOT) {
-    q.lo = bk.gl;
-    q.hi = bk.gu;
+    // the FP32 bracket, widened, confirmed by two FP64 counts (and widened
+    // further until they hold), inside the block's Gershgorin bracket
+    q.plo = fmax(v.lo[w], bk.gl);
+    q.phi = fmin(v.hi[w], bk.gu);
+    q.delta = kRoot32Margin * fmax(fabs(q.plo), fabs(q.phi)) + (q.phi - q.plo) + 4.0 * rn.pivmin;
+    q.lo = fmax(q.plo - q.delta, bk.gl);
+    q.hi = fmin(q.phi + q.delta, bk.gu);
+    q.phase = PH_VERIFY;
   } else if (MODE == MODE_REFINE) {
     // the parent bracket in child coordinates, widened by delta until two
     // counts confirm it
@@ -216,6 +301,11 @@ __device__ __forceinline__ bool iv_update(const Dev& v, int T, double rtol, int 
         q.delta *= 4.0;
         q.lo = q.plo - q.delta;
         q.hi = q.phi + q.delta;
+        if (MODE == MODE_ROOT) {  // never beyond the confirmed Gershgorin bracket
+          const Block& bk = v.blk[v.node[v.snode[q.slot]].block];
+          q.lo = fmax(q.lo, bk.gl);
+          q.hi = fmin(q.hi, bk.gu);
+        }
         if (q.tries > 48) {  // give up confirming; bisect what we have
           set_status(v.ctl, MRRR_ERR_NOCONV);
           diag(v.ctl, DIAG_REFINE_BRACKET);
@@ -350,26 +440,32 @@ __global__ void __launch_bounds__(kEngThreads, kEngCtasPerSm) k_engine(Dev v) {
 }
 
 template <int MODE>
-void launch_engine_mode(const Dev& v, const Grid& g, cudaStream_t s) {
+void launch_engine_mode(const Dev& v, const Grid& g, cudaStream_t s, int64_t n_total) {
   k_list_reset<<<1, 32, 0, s>>>(v);
   count_launch();
   k_list<MODE><<<g.slot_blocks, 128, 0, s>>>(v);
   count_launch();
+  if (MODE == MODE_ROOT) {
+    k_root32_copy<<<g.slot_blocks, 256, 0, s>>>(v, n_total);
+    count_launch();
+    k_root32<<<g.slot_blocks, 128, 0, s>>>(v);
+    count_launch();
+  }
   k_engine<MODE><<<g.nsm * max(1, min(kEngCtasPerSm, v.engine_ctas)), kEngThreads, 0, s>>>(v);
   count_launch();
 }
 
 }  // namespace
 
-void launch_engine(const Dev& v, int mode, const Grid& g, cudaStream_t s) {
+void launch_engine(const Dev& v, int mode, const Grid& g, cudaStream_t s, int64_t n_total) {
   if (mode == 0)
-    launch_engine_mode<MODE_ROOT>(v, g, s);
+    launch_engine_mode<MODE_ROOT>(v, g, s, n_total);
   else if (mode == 1)
-    launch_engine_mode<MODE_PREREFINE>(v, g, s);
+    launch_engine_mode<MODE_PREREFINE>(v, g, s, n_total);
   else if (mode == 2)
-    launch_engine_mode<MODE_REFINE>(v, g, s);
+    launch_engine_mode<MODE_REFINE>(v, g, s, n_total);
   else
-    launch_engine_mode<MODE_FINAL>(v, g, s);
+    launch_engine_mode<MODE_FINAL>(v, g, s, n_total);
 }
 
 }  // namespace mrrr

@@ -68,7 +68,7 @@ void launch_level_children(const Dev& v, int level, const Grid& g, cudaStream_t 
 
 // interval engine: mode 0 root bisection, 1 cluster pre-refinement in the
 // parent, 2 refinement in the child (see mrrr_engine.cu)
-void launch_engine(const Dev& v, int mode, const Grid& g, cudaStream_t s);
+void launch_engine(const Dev& v, int mode, const Grid& g, cudaStream_t s, int64_t n_total = 0);
 
 // eigenvectors (twisted factorization + Rayleigh-quotient correction),
 // normalisation and ordering of split problems

@@ -415,7 +415,7 @@ void launch_setup(const Dev& v, const ProblemArgs& a, int64_t n_total, const Gri
   k_root<<<std::max(pb, 1), 128, 0, s>>>(v);
   count_launch();
   mark_stage("root", s);
-  launch_engine(v, 0, g, s);
+  launch_engine(v, 0, g, s, n_total);
   mark_stage("bisect_root", s);
   k_rank<<<g.slot_blocks, g.tpb, 0, s>>>(v);
   count_launch();
