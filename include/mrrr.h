@@ -8,7 +8,7 @@
  * L0 D0 L0^T = T - sigma I, bisection for eigenvalue approximations,
  * classification into singletons and clusters by relative gap (tol 1e-3),
  * child representations Lc Dc Lc^T = L0 D0 L0^T - sigma_c I for clusters,
- * recursion, and eigenvectors by one step of inverse iteration with a
+ * recursion, and the vector of each singleton from a single solve with a
  * twisted factorization (Eq. errorangle).  The problem statement -- all or an
  * index subset il..iu of the eigenpairs -- is the paper's (Sec. 1.1,
  * Sec. 2.3, Sec. 5).  The accuracy goals are Eqs. Tresnorm / Torthogo

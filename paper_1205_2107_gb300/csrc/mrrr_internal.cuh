@@ -136,7 +136,7 @@ struct Dev {
   // slots (structure of arrays)
   double* lo;
   double* hi;
-  double* gap;        // absolute gap of a singleton (for the RQI stop test)
+  double* gap;        // absolute gap of a singleton or fallback slot to its neighbours
   double* wval;       // final eigenvalue (scaled, absolute)
   double* znrm2;      // squared norm of the unnormalised vector
   int* snode;

@@ -67,10 +67,11 @@ void launch_level_classify(const Dev& v, int level, const Grid& g, cudaStream_t 
 void launch_level_children(const Dev& v, int level, const Grid& g, cudaStream_t s);
 
 // interval engine: mode 0 root bisection, 1 cluster pre-refinement in the
-// parent, 2 refinement in the child (see mrrr_engine.cu)
+// parent, 2 refinement in the child, 3 singletons to full accuracy (see
+// mrrr_engine.cu); n_total sizes the FP32 root copy of mode 0
 void launch_engine(const Dev& v, int mode, const Grid& g, cudaStream_t s, int64_t n_total = 0);
 
-// eigenvectors (twisted factorization + Rayleigh-quotient correction),
+// eigenvectors (one twisted factorization each), the orthogonality safeguard,
 // normalisation and ordering of split problems
 void launch_vectors(const Dev& v, const Grid& g, cudaStream_t s);
 
