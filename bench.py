@@ -319,12 +319,13 @@ def run_ours(args, rank: int, world: int):
         e2e_step(check=True)
     barrier()
     e2e_times = []
-    for _ in range(args.steps):
-        flush.zero_()
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        e2e_step(check=False)
-        e2e_times.append(time.perf_counter() - t0)
+    with ClockSampler(local) as clk_e2e:
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            e2e_step(check=False)
+            e2e_times.append(time.perf_counter() - t0)
     e2e_value = whole_job_rate(pairs_per_step, args.steps, max_over_ranks(1e3 * sum(e2e_times), world, dev), world)
     del hz
 
@@ -367,7 +368,8 @@ def run_ours(args, rank: int, world: int):
                        "l2": "flushed before each step (256 MB write); Z output 3.2 GB per matrix",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "clocks": clocks, "gpu_launches": launches,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "ms_per_step": [round(1e3 * t, 1) for t in e2e_times], "clocks": clk_e2e.summary()},
             "roofline": roof, "path_roofline": path_roof, "cpu_baseline": cpu,
             "batched": side["batched"] if side else None, "adjoint": side["adjoint"] if side else None,
             "stages_ms_per_step": {k: v / args.steps for k, v in sorted(stage_ms.items())}}
