@@ -124,13 +124,6 @@ def default_plan(device: torch.device | None = None) -> Plan:
     return _default_plans[idx]
 
 
-def _finish(plan: Plan, where: str, check: bool) -> dict | None:
-    if not check:
-        return None
-    info = plan.info()
-    return info
-
-
 def _run_with_retry(plan: Plan, call, where: str, check: bool):
     """Run ``call(ws, ws_bytes)``; on a full node table or representation
     pool grow the plan's capacities to what the solve reported and rerun."""

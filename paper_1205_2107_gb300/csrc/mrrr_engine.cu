@@ -6,19 +6,21 @@
 // One launch works on one list of intervals (slot indices), built per mode
 // by k_list and split into long intervals (many halvings to go) and short
 // ones; the long ones run first.  The multisection width T (a power of two,
-// 1..32) follows from each part's length and the number of resident lanes: with few intervals each
-// gets T lanes that evaluate T interior points per pass over the
-// representation (log2(T+1) bits per pass instead of one, which shortens the
-// chain of dependent passes); with many intervals T = 1 and no work is
-// duplicated.  A warp holds 32/T lane groups and takes 32/T consecutive
-// list entries at a time (atomic counter) once all its groups are done.  Every lane streams its node's (D, LLD)
-// rows from L1/L2 with a register prefetch; the lanes of a group read the
-// same rows.  The Sturm counts are the division-free recurrence of
-// count_step().
+// 1..32) follows from each part's length and the number of resident lanes:
+// with few intervals each gets T lanes that evaluate T interior points per
+// pass over the representation (log2(T+1) bits per pass instead of one,
+// which shortens the chain of dependent passes); with many intervals T = 1
+// and no work is duplicated.  A warp holds 32/T lane groups and takes 32/T
+// consecutive list entries at a time (atomic counter) once all its groups
+// are done.  Every lane streams its node's (D, LLD) rows from L1/L2 with a
+// register prefetch; the lanes of a group read the same rows.  The Sturm
+// counts are the division-free recurrence of count_step().  Root intervals
+// are first narrowed in FP32 (k_root32) and confirmed in FP64.
 //
 // Modes:
-//   ROOT       root representation of a block, from its Gershgorin bracket,
-//              to the classification accuracy rtol;
+//   ROOT       root representation of a block, from the FP32 bracket (or,
+//              if two FP64 counts reject it, the Gershgorin bracket), to the
+//              classification accuracy rtol;
 //   PREREFINE  the two end members of a new cluster, in the PARENT's
 //              representation, to the cluster accuracy (so that the child
 //              shift can be placed right at the cluster's end);

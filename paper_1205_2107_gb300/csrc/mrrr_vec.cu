@@ -1,8 +1,9 @@
 // mrrr_vec.cu -- eigenvectors of singletons by one twisted factorization each
 // on the node's representation (Sec. 3.1.1: a singleton's vector is computed
 // in isolation from its representation, with the error bound of the
-// eigenvector-angle inequality), the normalisation of the columns of Z, and
-// the ordering of split problems.
+// eigenvector-angle inequality), the normalisation of the columns of Z, an
+// orthogonality safeguard between neighbouring columns, and the ordering of
+// split problems.
 //
 // The eigenvalue comes in bisected to full relative accuracy (the interval
 // engine's FINAL mode), so a single twisted factorization suffices.
