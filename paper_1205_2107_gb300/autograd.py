@@ -19,20 +19,27 @@ from . import api
 
 
 class EighTridiagonal(torch.autograd.Function):
-    """One problem: (d, e) -> (W, Z), all eigenpairs."""
+    """One problem: (d, e) -> (W, Z), all eigenpairs.  With recompute, only
+    (d, e) are kept for the backward pass, which solves again (the solver is
+    deterministic, so W and Z come out identical)."""
 
     @staticmethod
-    def forward(ctx, d, e, tau_rel=0.0, plan=None):
+    def forward(ctx, d, e, tau_rel=0.0, plan=None, recompute=False):
         W, Z = api.eigh_tridiagonal(d.detach(), e.detach(), plan=plan)
         ctx.tau_rel = float(tau_rel)
         ctx.plan = plan
         ctx.e_numel = e.numel()
-        ctx.save_for_backward(W, Z)
+        ctx.recompute = bool(recompute)
+        ctx.save_for_backward(*((d.detach(), e.detach()) if recompute else (W, Z)))
         return W, Z
 
     @staticmethod
     def backward(ctx, gW, gZ):
-        W, Z = ctx.saved_tensors
+        if ctx.recompute:
+            d, e = ctx.saved_tensors
+            W, Z = api.eigh_tridiagonal(d, e, plan=ctx.plan)
+        else:
+            W, Z = ctx.saved_tensors
         n = W.numel()
         layout = api.BatchLayout([n], W.device)
         Zflat = Z.t().contiguous().view(-1)  # column-major storage of Z
@@ -42,14 +49,16 @@ class EighTridiagonal(torch.autograd.Function):
         ge = torch.zeros(ctx.e_numel, dtype=dbar.dtype, device=dbar.device)
         m = min(ctx.e_numel, max(n - 1, 0))
         ge[:m] = ebar[:m]
-        return dbar, ge, None, None
+        return dbar, ge, None, None, None
 
 
 class EighTridiagonalBatched(torch.autograd.Function):
-    """A batch packed by an all-eigenpair BatchLayout: (d, e) -> packed (W, Z)."""
+    """A batch packed by an all-eigenpair BatchLayout: (d, e) -> packed (W, Z).
+    With recompute, the backward pass solves the batch again instead of
+    keeping Z (sum n_p^2 doubles) alive between the passes."""
 
     @staticmethod
-    def forward(ctx, d, e, layout, tau_rel=0.0, plan=None):
+    def forward(ctx, d, e, layout, tau_rel=0.0, plan=None, recompute=False):
         if not layout.all:
             raise ValueError("autograd needs all eigenpairs of every problem")
         W, Z = api.eigh_tridiagonal_batched(d.detach(), e.detach(), layout, plan=plan)
@@ -59,27 +68,35 @@ class EighTridiagonalBatched(torch.autograd.Function):
         ctx.tau_rel = float(tau_rel)
         ctx.plan = plan
         ctx.e_numel = e.numel()
-        ctx.save_for_backward(W, Z)
+        ctx.recompute = bool(recompute)
+        ctx.save_for_backward(*((d.detach(), e.detach()) if recompute else (W, Z)))
         return W, Z
 
     @staticmethod
     def backward(ctx, gW, gZ):
-        W, Z = ctx.saved_tensors
+        if ctx.recompute:
+            d, e = ctx.saved_tensors
+            W, Z = api.eigh_tridiagonal_batched(d, e, ctx.layout, plan=ctx.plan)
+            W, Z = W[:ctx.layout.k_total], Z[:ctx.layout.z_total]
+        else:
+            W, Z = ctx.saved_tensors
         Wb = gW.contiguous() if gW is not None else None
         Zb = gZ.contiguous() if gZ is not None else None
         dbar, ebar = api.eigh_tridiagonal_backward(W, Z, Wb, Zb, ctx.layout, tau_rel=ctx.tau_rel, plan=ctx.plan)
         ge = torch.zeros(ctx.e_numel, dtype=dbar.dtype, device=dbar.device)
         m = min(ctx.e_numel, ebar.numel())
         ge[:m] = ebar[:m]
-        return dbar, ge, None, None, None
+        return dbar, ge, None, None, None, None
 
 
-def eigh_tridiagonal_autograd(d: torch.Tensor, e: torch.Tensor, *, tau_rel: float = 0.0, plan=None):
+def eigh_tridiagonal_autograd(d: torch.Tensor, e: torch.Tensor, *, tau_rel: float = 0.0, plan=None,
+                              recompute: bool = False):
     """All eigenpairs (W, Z) of one tridiagonal, differentiable in (d, e)."""
-    return EighTridiagonal.apply(d, e, tau_rel, plan)
+    return EighTridiagonal.apply(d, e, tau_rel, plan, recompute)
 
 
 def eigh_tridiagonal_batched_autograd(d: torch.Tensor, e: torch.Tensor, layout, *, tau_rel: float = 0.0,
-                                      plan=None):
-    """Packed all-eigenpair solution of a batch, differentiable in (d, e)."""
-    return EighTridiagonalBatched.apply(d, e, layout, tau_rel, plan)
+                                      plan=None, recompute: bool = False):
+    """Packed all-eigenpair solution of a batch, differentiable in (d, e);
+    recompute trades a second solve for not keeping Z between the passes."""
+    return EighTridiagonalBatched.apply(d, e, layout, tau_rel, plan, recompute)

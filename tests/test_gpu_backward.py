@@ -152,3 +152,31 @@ def test_full_size_adjoint_batch_sampled():
         od, oe = oracle_gradient(d[p], e[p], w[p], C[p])
         assert_close_grad(gd[p], od, f"dbar problem {p}")
         assert_close_grad(ge[p, :-1], oe, f"ebar problem {p}")
+
+
+def test_recompute_gives_the_same_gradient():
+    """recompute=True solves again in the backward pass instead of keeping Z;
+    the solver is deterministic, so the gradients agree bit for bit."""
+    d, e, w, C = inputs.adjoint_case(batch=8, n=200, seed=21)
+    batch, n = d.shape
+    lay = api.BatchLayout([n] * batch, "cuda")
+    grads = []
+    for recompute in (False, True):
+        dt = _dev(d.reshape(-1)).requires_grad_(True)
+        et = _dev(e.reshape(-1)).requires_grad_(True)
+        W, Z = autograd.eigh_tridiagonal_batched_autograd(dt, et, lay, recompute=recompute)
+        Zb = Z.view(batch, n, n)
+        Ct = _dev(C).transpose(1, 2)
+        loss = (_dev(w).reshape(-1) * W).sum() + ((Ct * Zb).sum(2) ** 2).sum()
+        loss.backward()
+        grads.append((dt.grad.clone(), et.grad.clone()))
+    assert torch.equal(grads[0][0], grads[1][0]) and torch.equal(grads[0][1], grads[1][1])
+    # the single-problem function too
+    g1 = []
+    for recompute in (False, True):
+        dt = _dev(d[0]).requires_grad_(True)
+        et = _dev(e[0][:-1]).requires_grad_(True)
+        W, Z = autograd.eigh_tridiagonal_autograd(dt, et, recompute=recompute)
+        ((_dev(w[0]) * W).sum() + ((_dev(C[0]) * Z).sum(0) ** 2).sum()).backward()
+        g1.append((dt.grad.clone(), et.grad.clone()))
+    assert torch.equal(g1[0][0], g1[1][0]) and torch.equal(g1[0][1], g1[1][1])
