@@ -120,3 +120,22 @@ def test_full_size_batch_4096_sampled():
     for p in sorted(set(rng.integers(0, len(sizes), 6).tolist()) | {int(np.argmax(sizes))}):
         check_problem(d[off[p]:off[p + 1]], e[off[p]:off[p + 1]], Ws[p], Zs[p], 1, sizes[p],
                       compare_vectors=False)
+
+
+def test_batch_with_empty_problems():
+    """Problems of order 0 inside a batch produce nothing and disturb nothing."""
+    sizes = [0, 5, 0, 17, 1, 0]
+    d, e, off = inputs.batched_uniform(sizes, 23)
+    lay = api.BatchLayout(sizes, "cuda")
+    W, Z = api.eigh_tridiagonal_batched(_dev(d), _dev(e), lay)
+    Ws, Zs = lay.unpack(W, Z)
+    for p, n in enumerate(sizes):
+        assert Ws[p].numel() == n and tuple(Zs[p].shape) == (n, n)
+        if n:
+            check_problem(d[off[p]:off[p + 1]], e[off[p]:off[p + 1]], Ws[p], Zs[p], 1, n)
+
+
+def test_single_problem_of_order_zero():
+    W, Z = api.eigh_tridiagonal(torch.zeros(0, dtype=torch.float64, device="cuda"),
+                                torch.zeros(0, dtype=torch.float64, device="cuda"))
+    assert W.numel() == 0 and Z.numel() == 0
