@@ -1,0 +1,67 @@
+"""Host-side logic that needs no GPU: batch packing, the seeded input
+generators, and the benchmark's oracle sampling."""
+import os
+import sys
+
+import numpy as np
+import pytest
+import torch
+
+from paper_1205_2107_gb300 import inputs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_batch_layout_offsets_and_unpack():
+    from paper_1205_2107_gb300.api import BatchLayout
+    sizes = [3, 0, 5, 1]
+    lay = BatchLayout(sizes, "cpu")
+    assert lay.offsets_host == [0, 3, 3, 8, 9]
+    assert lay.w_offsets_host == [0, 3, 3, 8, 9]
+    assert lay.z_offsets_host == [0, 9, 9, 34, 35]
+    assert lay.n_total == 9 and lay.k_total == 9 and lay.z_total == 35 and lay.n_max == 5 and lay.all
+    W = torch.arange(9, dtype=torch.float64)
+    Z = torch.arange(35, dtype=torch.float64)
+    Ws, Zs = lay.unpack(W, Z)
+    assert [w.numel() for w in Ws] == sizes
+    # problem 2: column-major 5 x 5 block at offset 9; Z_p[i, j] = Z[9 + j * 5 + i]
+    assert Zs[2][1, 3].item() == 9 + 3 * 5 + 1
+    assert tuple(Zs[1].shape) == (0, 0)
+
+
+def test_batch_layout_subsets():
+    from paper_1205_2107_gb300.api import BatchLayout
+    lay = BatchLayout([10, 4], "cpu", il=[2, 1], iu=[5, 4])
+    assert lay.ks == [4, 4] and not lay.all
+    assert lay.z_offsets_host == [0, 40, 56]
+    assert lay.il.tolist() == [2, 1] and lay.iu.tolist() == [5, 4]
+
+
+def test_generators_are_seeded_and_shaped():
+    d1, e1 = inputs.uniform(100, 7)
+    d2, e2 = inputs.uniform(100, 7)
+    assert np.array_equal(d1, d2) and np.array_equal(e1, e2) and e1.shape == (99,)
+    d, e = inputs.wilkinson_plus(21)
+    assert d[0] == 10 and d[10] == 0 and np.all(e == 1.0)
+    d, e = inputs.glued_wilkinson(3, glue=1e-10)
+    assert d.shape == (63,) and e[20] == 1e-10 and e[41] == 1e-10 and e[19] == 1.0
+    sizes = inputs.batch_sizes(4096)
+    assert sizes.min() >= 32 and sizes.max() <= 2048 and len(sizes) == 4096
+    d, e, off = inputs.batched_uniform([4, 0, 3], 1)
+    assert off.tolist() == [0, 4, 4, 7] and e[3] == 0.0 and e[6] == 0.0
+    d, e, w, C = inputs.adjoint_case(batch=2, n=8, seed=3)
+    assert d.shape == (2, 8) and C.shape == (2, 8, 8) and np.all(e[:, -1] == 0.0)
+    d, e = inputs.large_uniform(1000, 50000)
+    assert d.min() >= 0 and d.max() <= 1 and e.min() >= 0 and e.max() <= 1e-2
+
+
+def test_bench_oracle_windows():
+    sys.path.insert(0, ROOT)
+    import bench
+    mats = [("a", *inputs.uniform(300, 1)), ("b", *inputs.uniform(200, 2))]
+    jobs = bench.oracle_windows(mats, 3, offset=1)
+    assert len(jobs) == 6
+    for d, e, il, iu in jobs:
+        assert 1 <= il <= iu <= len(d) and iu - il + 1 == bench.WINDOW
+    done, secs = bench.oracle_sample(jobs[:2], 2)
+    assert done == 2 * bench.WINDOW and secs > 0
