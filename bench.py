@@ -40,6 +40,7 @@ FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070  # SMs x DFMA/clk/SM x flops/DFMA x GHz (
 BISECT_FLOPS_PER_ROW = 4 * 32
 PATH_FLOPS_PER_ROW = BISECT_FLOPS_PER_ROW + 15
 ENGINE_STAGES = ("bisect_root", "prerefine", "refine", "final_bisect")
+DIV_COST_DFMA = 9.0  # measured: DFMA 602 G/s, DDIV 67 G/s on this part
 
 
 def _hbm_gbs() -> float:
@@ -344,8 +345,12 @@ def run_ours(args, rank: int, world: int):
     t_flop = PATH_FLOPS_PER_ROW * nk / (FP64_PEAK_GFLOPS * 1e9)
     t_hbm = 8.0 * nk / (HBM_GBS * 1e9)
     t_roof_ms = 1e3 * max(t_flop, t_hbm)
+    # division-weighted: the model's 2 divides per row of the vector step count
+    # DIV_COST_DFMA flop-equivalents each instead of 1 (measured DDIV vs DFMA rate)
+    t_div = (PATH_FLOPS_PER_ROW + 2 * (DIV_COST_DFMA - 1)) * nk / (FP64_PEAK_GFLOPS * 1e9)
     path_roof = {"t_roof_ms": t_roof_ms, "t_step_ms": total_ms / args.steps,
                  "frac": t_roof_ms / (total_ms / args.steps), "bound": "alu" if t_flop >= t_hbm else "hbm",
+                 "frac_division_weighted": 1e3 * max(t_div, t_hbm) / (total_ms / args.steps),
                  "model": "143 n flops + 8 n bytes per eigenpair", "hbm_gbs": HBM_GBS}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
