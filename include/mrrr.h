@@ -93,7 +93,8 @@ typedef struct mrrr_info {
   int depth;               /* deepest cluster level reached                 */
   int64_t nodes;           /* cluster nodes created (roots excluded)        */
   int64_t pool_rows_used;  /* child-representation rows needed              */
-  int64_t fallbacks;       /* eigenvalues that took the depth/shift fallback */
+  int64_t fallbacks;       /* eigenvalues whose vectors were taken at a parent
+                              node (depth limit or full node table/pool)    */
   int64_t twisted_solves;  /* twisted factorizations solved, all vectors    */
   int64_t levels;          /* cluster levels processed                      */
   int64_t diag[12];        /* event counters: [0] root-shift retries exhausted,
@@ -135,8 +136,9 @@ mrrr_status mrrr_workspace_size(const mrrr_plan* plan, int batch, int64_t n_tota
  *   workspace  device, ws_bytes >= mrrr_workspace_size(plan, 1, n, k, n)
  *   stream     CUDA stream for every launch
  * Returns MRRR_ERR_ARG / MRRR_ERR_WORKSPACE for bad host-side arguments.
- * The call synchronises the stream once per cluster level; device-side
- * errors are read with mrrr_get_status.
+ * Without use_graph the call synchronises the stream once per cluster
+ * level; with use_graph it enqueues one graph launch (capturing it first for
+ * a new call signature).  Device-side errors are read with mrrr_get_status.
  */
 mrrr_status mrrr_stein(mrrr_plan* plan, int n, const double* d, const double* e, int il, int iu,
                        double* W, double* Z, int64_t ldz, void* workspace, size_t ws_bytes,
@@ -154,7 +156,10 @@ mrrr_status mrrr_stein(mrrr_plan* plan, int n, const double* d, const double* e,
  *              column-major block at Z + z_off[p] with leading dimension n_p
  *   n_max      largest n_p; k_total = sum of k_p (workspace sizing)
  * Argument ranges inside the device arrays are checked on the GPU
- * (MRRR_ERR_ARG in the status word).
+ * (MRRR_ERR_ARG in the status word).  Not in the paper: every problem is
+ * solved by the method of mrrr_stein (Sec. 3.1.1); the problems share the
+ * launches, the work lists and the cluster levels.  Synchronisation as in
+ * mrrr_stein (use_graph captures the whole batched solve).
  */
 mrrr_status mrrr_stein_batched(mrrr_plan* plan, int batch, const int64_t* d_off, const double* d,
                                const double* e, const int* il, const int* iu, double* W,
