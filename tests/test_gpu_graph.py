@@ -61,3 +61,28 @@ def test_autotune_keeps_results_valid():
         tn = float(Ws[p].abs().max())
         assert float(checks.residual_cols(d[off[p]:off[p + 1]], ep, Ws[p], Zs[p]).max()) <= 20 * n * EPS * tn
         assert checks.orthogonality(Zs[p]) <= 20 * n * EPS
+
+
+def test_single_problem_graph_replay_matches_direct():
+    d, e = inputs.glued_wilkinson(20)
+    dd = torch.as_tensor(d, device="cuda")
+    ee = torch.as_tensor(np.append(e, 0.0), device="cuda")
+    W0, Z0 = api.eigh_tridiagonal(dd, ee, plan=api.Plan(0))
+    gplan = api.Plan(0, use_graph=1)
+    for _ in range(3):  # capture, then replays (new output buffers: new signatures)
+        W1, Z1 = api.eigh_tridiagonal(dd, ee, plan=gplan)
+        assert torch.equal(W0, W1) and torch.equal(Z0, Z1)
+    W2 = api.eigh_tridiagonal(dd, ee, 5, 40, plan=gplan, vectors=False)
+    assert torch.equal(W2, W0[4:40])
+
+
+def test_autotune_then_graph_recaptures():
+    sizes, d, e, off, lay = _batch(48, 14, nmax=400)
+    plan = api.Plan(0, use_graph=1)
+    W0, Z0 = api.eigh_tridiagonal_batched(d, e, lay, plan=api.Plan(0))
+    api.autotune_batched(d, e, lay, plan=plan)
+    W1, Z1 = api.eigh_tridiagonal_batched(d, e, lay, plan=plan)
+    # a different launch shape may change rounding inside the bisection, so
+    # compare to the accuracy goals, not bit for bit
+    tn = float(W0[:lay.k_total].abs().max())
+    assert float((W1[:lay.k_total] - W0[:lay.k_total]).abs().max()) <= 4 * max(sizes) * EPS * tn
