@@ -41,6 +41,7 @@ BISECT_FLOPS_PER_ROW = 4 * 32
 PATH_FLOPS_PER_ROW = BISECT_FLOPS_PER_ROW + 15
 ENGINE_STAGES = ("bisect_root", "prerefine", "refine", "final_bisect")
 DIV_COST_DFMA = 9.0  # measured: DFMA 602 G/s, DDIV 67 G/s on this part
+ENGINE_BYTES_PER_CHILD_ROW = 32  # engine DRAM traffic per child-representation row (ncu, W+ n=2001)
 
 
 def _hbm_gbs() -> float:
@@ -278,11 +279,13 @@ def run_ours(args, rank: int, world: int):
                 for k, v in prof["stages"].items():
                     stage_ms[k] = stage_ms.get(k, 0.0) + v
     barrier()
+    child_rows = 0
     for plan in plans:
         info = plan.info()
         if info["status"] != 0:
             raise SystemExit(f"solver reported status {info['status']} ({info})")
         plan.set_timing(False)
+        child_rows += int(info["pool_rows_used"]) - sum(sizes)
     total_ms = max_over_ranks(sum(times), world, dev)
     value = whole_job_rate(pairs_per_step, args.steps, total_ms, world)
 
@@ -339,7 +342,11 @@ def run_ours(args, rank: int, world: int):
         achieved = BISECT_FLOPS_PER_ROW * nk / (engine_ms * 1e-3) / 1e9
         roof = {"bound": "alu", "kernel": "k_engine (interval bisection, all modes)", "achieved": achieved,
                 "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS,
-                "traffic": None, "engine_ms_per_step": engine_ms,
+                "traffic": ENGINE_BYTES_PER_CHILD_ROW * max(child_rows, 0),
+                "traffic_source": "DRAM bytes per step, scaled from the ncu capture of W+ n=2001 (64.9 MB over its "
+                                  "6 engine launches = 31 bytes per child-representation row: refine and final "
+                                  "each read every child row once) by the step's child rows",
+                "engine_ms_per_step": engine_ms,
                 "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz (max SM clock)"}
     # whole path against T_roof = max(F / P_fp64, 8 n k / BW), F = 143 n k
     t_flop = PATH_FLOPS_PER_ROW * nk / (FP64_PEAK_GFLOPS * 1e9)
