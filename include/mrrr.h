@@ -203,6 +203,7 @@ mrrr_status mrrr_autotune_batched(mrrr_plan* plan, int batch, const int64_t* d_o
  *   dbar_j = Tbar(j,j),  ebar_j = Tbar(j,j+1) + Tbar(j+1,j),
  * so dbar_j = sum_i Wbar_i Z(j,i)^2 + ..., ebar_j = 2 sum_i Wbar_i Z(j,i)
  * Z(j+1,i) + ....  The two n^3 contractions run on the FP64 tensor cores.
+ *   batch      0..65535 (each problem is one index of a grid dimension)
  *   d_off      device int64[batch+1] as in mrrr_stein_batched; W and Wbar
  *              use the same packing (n_p values of problem p at d_off[p])
  *   Z, Zbar    device; problem p's n_p x n_p column-major block starts at

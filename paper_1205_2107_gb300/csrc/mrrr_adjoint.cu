@@ -301,6 +301,7 @@ mrrr_status mrrr_backward(mrrr_plan* plan, int batch, const int64_t* d_off, cons
                           const double* Wbar, const double* Zbar, double tau_rel, int n_max, int64_t z_total,
                           double* dbar, double* ebar, void* workspace, size_t ws_bytes, mrrr_stream stream) {
   if (!plan || batch < 0 || n_max < 0 || z_total < 0 || !(tau_rel >= 0.0)) return MRRR_ERR_ARG;
+  if (batch > 65535) return MRRR_ERR_ARG;  // one grid z (or y) index per problem
   if (batch == 0 || n_max == 0) return MRRR_OK;
   if (!d_off || !W || !Z || !dbar || !ebar) return MRRR_ERR_ARG;
   size_t need = 0;

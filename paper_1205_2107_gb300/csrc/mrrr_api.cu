@@ -21,6 +21,16 @@ struct GraphKey {
   int64_t opt_version;
 };
 
+// Field by field: the structs have padding, whose bytes are not part of
+// the key.
+static bool same_key(const GraphKey& x, const GraphKey& y) {
+  const mrrr::ProblemArgs &a = x.a, &b = y.a;
+  return a.batch == b.batch && a.d_off == b.d_off && a.il == b.il && a.iu == b.iu && a.w_off == b.w_off &&
+         a.z_off == b.z_off && a.n == b.n && a.il1 == b.il1 && a.iu1 == b.iu1 && a.ldz == b.ldz && x.d == y.d &&
+         x.e == y.e && x.ws == y.ws && x.W == y.W && x.Z == y.Z && x.n_total == y.n_total &&
+         x.k_total == y.k_total && x.n_max == y.n_max && x.ws_bytes == y.ws_bytes && x.opt_version == y.opt_version;
+}
+
 struct mrrr_plan {
   mrrr_options opt;
   int device;
@@ -254,6 +264,9 @@ mrrr_status solve(mrrr_plan* p, const ProblemArgs& a, const double* d, const dou
     tm->mark("classify", s);
     if (cudaMemcpyAsync(p->host_ctl, v.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {
+      tm->on = false;
+      tm->finish();  // only releases the events recorded so far
+      tm->on = timing_was;
       set_stage_timer(nullptr);
       return MRRR_ERR_CUDA;
     }
@@ -290,7 +303,7 @@ mrrr_status solve_graph(mrrr_plan* p, const ProblemArgs& a, const double* d, con
   k.n_max = n_max;
   k.ws_bytes = ws_bytes;
   k.opt_version = p->opt_version;
-  if (!p->have_graph || std::memcmp(&k, &p->key, sizeof(k)) != 0) {
+  if (!p->have_graph || !same_key(k, p->key)) {
     if (p->have_graph) {
       cudaGraphExecDestroy(p->exec);
       p->have_graph = false;
@@ -308,7 +321,7 @@ mrrr_status solve_graph(mrrr_plan* p, const ProblemArgs& a, const double* d, con
     const cudaError_t ie = cudaGraphInstantiate(&p->exec, graph, 0);
     cudaGraphDestroy(graph);
     if (ie != cudaSuccess) return MRRR_ERR_CUDA;
-    std::memcpy(&p->key, &k, sizeof(k));
+    p->key = k;
     p->have_graph = true;
     p->graph_launches = p->timer.launches;
   }
@@ -463,7 +476,11 @@ mrrr_status mrrr_autotune_batched(mrrr_plan* plan, int batch, const int64_t* d_o
   const bool timing = plan->timer.on;
   plan->timer.on = false;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return MRRR_ERR_CUDA;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    plan->timer.on = timing;
+    return MRRR_ERR_CUDA;
+  }
   std::memset(out, 0, sizeof(*out));
   double best = INFINITY;
   mrrr_status st = MRRR_OK;
