@@ -166,6 +166,39 @@ def calibrated_windows(mats, nthreads: int, seconds: float) -> int:
     return int(np.clip(round(want), 1, 4096))
 
 
+def host_cpu() -> dict:
+    """The host's CPU model and logical core count, recorded beside the
+    oracle timings (x86 /proc/cpuinfo has a model name; on Arm lscpu gives
+    one, else the implementer and part codes)."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            info = f.read()
+    except OSError:
+        info = ""
+    for line in info.splitlines():
+        if line.lower().startswith("model name"):
+            model = line.split(":", 1)[1].strip()
+            break
+    if model is None:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.startswith("Model name:"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except (OSError, subprocess.SubprocessError):
+            pass
+    if model is None:
+        codes = {}
+        for line in info.splitlines():
+            k, _, v = line.partition(":")
+            if k.strip() in ("CPU implementer", "CPU part") and k.strip() not in codes:
+                codes[k.strip()] = v.strip()
+        model = " ".join(f"{k} {v}" for k, v in codes.items()) or os.uname().machine
+    return {"model": model, "nproc": os.cpu_count()}
+
+
 def sample_text(windows: int, nmats: int, cores: int, secs: float) -> str:
     return (f"{windows} windows x {WINDOW} consecutive eigenpairs per matrix ({windows * WINDOW * nmats} "
             f"eigenpairs, spread over each spectrum) of the same two matrices: oracle bisection on T + "
@@ -194,7 +227,8 @@ def run_reference(args, rank: int, world: int):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                             "host": host_cpu()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -366,7 +400,7 @@ def run_ours(args, rank: int, world: int):
         windows = calibrated_windows(mats, cores, args.cpu_seconds)
         p, t = oracle_sample(oracle_windows(mats, windows, offset=1), cores)
         cpu = {"value": p / t, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": sample_text(windows, len(mats), cores, t)}
+               "sample": sample_text(windows, len(mats), cores, t), "host": host_cpu()}
     side = None
     if not args.no_side:
         side = side_by_side(args, dev, flush)

@@ -65,3 +65,11 @@ def test_bench_oracle_windows():
         assert 1 <= il <= iu <= len(d) and iu - il + 1 == bench.WINDOW
     done, secs = bench.oracle_sample(jobs[:2], 2)
     assert done == 2 * bench.WINDOW and secs > 0
+
+
+def test_bench_records_the_host_cpu():
+    sys.path.insert(0, ROOT)
+    import bench
+    h = bench.host_cpu()
+    assert isinstance(h["model"], str) and h["model"]
+    assert h["nproc"] == os.cpu_count() and h["nproc"] >= 1
