@@ -20,10 +20,10 @@
  *     bisection; Sec. 2.1 names the bisection + inverse iteration solver);
  *   - eigenvectors: classical inverse iteration (T - lambda I) z' = s z
  *     (Sec. 3.1, the inverse-iteration equation) with modified Gram-Schmidt
- *     re-orthogonalisation inside clusters, clusters being runs of
- *     eigenvalues closer than orfac*||T||, orfac = 1e-3 by default (Sec. 2.1,
- *     footnote on the orfac parameter).  This is the paper's "BI" method: slow
- *     but simple and independent of MRRR;
+ *     re-orthogonalisation inside clusters, clusters being runs of one
+ *     block's eigenvalues closer than orfac*||T_b||, orfac = 1e-3 by default
+ *     (Sec. 2.1, footnote on the orfac parameter).  This is the paper's "BI"
+ *     method: slow but simple and independent of MRRR;
  *   - a dense cyclic Jacobi solver for small n (brute force, used to pin the
  *     two methods above).
  *
@@ -33,6 +33,10 @@
  *   - bisection stops when the midpoint equals an endpoint in floating point
  *     or the width is at most 2 eps max(|lo|,|hi|);
  *   - ties between equal eigenvalues of different blocks are ordered by block;
+ *   - inverse iteration is done block by block with the block's own norm
+ *     ||T_b|| = max |eigenvalue of T_b| (reorthogonalisation threshold,
+ *     zero-pivot perturbation eps*||T_b||, growth test), on the block scaled
+ *     by the power of two that brings ||T_b|| into [1, 2);
  *   - inverse-iteration start vectors come from a splitmix64 stream seeded by
  *     the eigenvalue's position, so results are deterministic.
  *
@@ -250,6 +254,20 @@ static void bisect_task(void* vctx, int64_t item) {
   c->out[item].local = k;
 }
 
+/* a selected eigenvalue by (block, index within the block), for clustering */
+typedef struct {
+  int block;
+  int local;
+  int64_t pos; /* output position */
+} member_t;
+
+static int member_cmp(const void* pa, const void* pb) {
+  const member_t* a = (const member_t*)pa;
+  const member_t* b = (const member_t*)pb;
+  if (a->block != b->block) return a->block < b->block ? -1 : 1;
+  return a->local < b->local ? -1 : (a->local > b->local);
+}
+
 static int eig_cmp(const void* pa, const void* pb) {
   const eig_t* a = (const eig_t*)pa;
   const eig_t* b = (const eig_t*)pb;
@@ -337,7 +355,8 @@ static void lu_solve(const lu_t* f, double* x) {
       x[k + 1] -= f->mult[k] * x[k];
     }
   }
-  const double big = 0x1p900;
+  /* rescale before an entry passes 2^400: the 2-norm squares the entries */
+  const double big = 0x1p400;
   for (int k = m - 1; k >= 0; --k) {
     double v = x[k];
     if (k + 1 < m) v -= f->u1[k] * x[k + 1];
@@ -368,16 +387,30 @@ static uint64_t splitmix64(uint64_t* s) {
 
 /* Vectors of one cluster (consecutive eigenvalues mus[0..c) of one block):
    inverse iteration, each iterate re-orthogonalised (MGS, twice) against the
-   cluster's earlier vectors.  Output columns vecs[j*m ...]. */
-static void cluster_vectors(int m, const double* d, const double* es, int c, const double* mus,
+   cluster's earlier vectors.  Output columns vecs[j*m ...].  The block and
+   the shifts are first scaled by the power of two that brings the block's
+   norm tnorm into [1, 2): exact, leaves the vectors unchanged, and keeps the
+   zero-pivot perturbation eps*||T_b|| and the iterates in the normal range
+   for blocks of any magnitude. */
+static void cluster_vectors(int m, const double* d_in, const double* es_in, int c, const double* mus,
                             double tnorm, uint64_t seed, double* vecs) {
+  int kb = 0;
+  if (tnorm > 0 && isfinite(tnorm)) {
+    frexp(tnorm, &kb);
+    kb = 1 - kb;
+  }
+  double* d = (double*)malloc(sizeof(double) * m);
+  double* es = (double*)malloc(sizeof(double) * m);
+  for (int i = 0; i < m; ++i) d[i] = ldexp(d_in[i], kb);
+  for (int i = 0; i + 1 < m; ++i) es[i] = ldexp(es_in[i], kb);
+  tnorm = ldexp(tnorm, kb);
   lu_t f;
   lu_alloc(&f, m);
   double* x = (double*)malloc(sizeof(double) * m);
   double tiny = ORACLE_EPS * (tnorm > 0 ? tnorm : 1.0);
   double prev_mu = -INFINITY;
   for (int j = 0; j < c; ++j) {
-    double mu = mus[j];
+    double mu = ldexp(mus[j], kb);
     /* nearly equal shifts are pulled apart so each LU differs */
     double sep = 10.0 * ORACLE_EPS * fmax(fabs(mu), tiny);
     if (mu - prev_mu < sep) mu = prev_mu + sep;
@@ -407,6 +440,8 @@ static void cluster_vectors(int m, const double* d, const double* es, int c, con
     for (int i = 0; i < m; ++i) out[i] = x[i] / nx;
   }
   free(x);
+  free(d);
+  free(es);
   lu_free(&f);
 }
 
@@ -414,10 +449,11 @@ typedef struct {
   const double* d;
   const double* es;
   const int* starts;
-  const eig_t* sel; /* selected eigenvalues in output order */
-  const int64_t* cl_first;
+  const eig_t* sel;       /* selected eigenvalues in output order */
+  const int64_t* member;  /* output positions, grouped cluster by cluster */
+  const int64_t* cl_first; /* cluster -> first entry of member[] */
   const int64_t* cl_count;
-  double tnorm;
+  const double* bnorm;    /* per block: max |eigenvalue| of the block */
   double* Z;
   int64_t ldz;
   int n;
@@ -425,16 +461,16 @@ typedef struct {
 
 static void vec_task(void* vctx, int64_t cl) {
   vec_ctx* c = (vec_ctx*)vctx;
-  int64_t f = c->cl_first[cl];
+  const int64_t* pos = c->member + c->cl_first[cl];
   int cnt = (int)c->cl_count[cl];
-  int b = c->sel[f].block;
+  int b = c->sel[pos[0]].block;
   int s = c->starts[b], m = c->starts[b + 1] - s;
   double* mus = (double*)malloc(sizeof(double) * cnt);
   double* vecs = (double*)malloc(sizeof(double) * (int64_t)cnt * m);
-  for (int j = 0; j < cnt; ++j) mus[j] = c->sel[f + j].value;
-  cluster_vectors(m, c->d + s, c->es + s, cnt, mus, c->tnorm, 0x5EEDull + 7919ull * (uint64_t)f, vecs);
+  for (int j = 0; j < cnt; ++j) mus[j] = c->sel[pos[j]].value;
+  cluster_vectors(m, c->d + s, c->es + s, cnt, mus, c->bnorm[b], 0x5EEDull + 7919ull * (uint64_t)pos[0], vecs);
   for (int j = 0; j < cnt; ++j) {
-    double* col = c->Z + (f + j) * c->ldz;
+    double* col = c->Z + pos[j] * c->ldz;
     for (int i = 0; i < c->n; ++i) col[i] = 0.0;
     memcpy(col + s, vecs + (int64_t)j * m, sizeof(double) * m);
   }
@@ -496,35 +532,50 @@ int oracle_eigh(int n, const double* d, const double* e, int il, int iu, double 
   for (int j = 0; j < k; ++j) W[j] = sel[j].value;
 
   if (Z) {
-    /* clusters: runs (within one block, consecutive in output order) whose
-       consecutive gaps are at most orfac*||T|| */
+    /* Inverse iteration works block by block, so its norm is the block's:
+       ||T_b|| = max |eigenvalue of T_b| scales the reorthogonalisation
+       threshold orfac*||T_b||, the zero-pivot perturbation and the growth
+       test (as in the standard bisection + inverse iteration solvers). */
+    double* bnorm = (double*)calloc(nb, sizeof(double));
+    if (nb == 1) {
+      bnorm[0] = tnorm;
+    } else {
+      for (int64_t t = 0; t < nitems; ++t)
+        bnorm[all[t].block] = fmax(bnorm[all[t].block], fabs(all[t].value));
+    }
+    /* clusters: within each block, maximal runs of the block's selected
+       eigenvalues, taken in the block's own order, whose consecutive gaps
+       are at most orfac*||T_b||.  With several blocks a cluster's output
+       positions need not be contiguous (eigenvalues of other blocks may lie
+       between its members), so the members are listed by position. */
+    member_t* ord = (member_t*)malloc(sizeof(member_t) * k);
+    for (int j = 0; j < k; ++j) ord[j].block = sel[j].block, ord[j].local = sel[j].local, ord[j].pos = j;
+    qsort(ord, k, sizeof(member_t), member_cmp);
+    int64_t* member = (int64_t*)malloc(sizeof(int64_t) * k);
     int64_t* cl_first = (int64_t*)malloc(sizeof(int64_t) * k);
     int64_t* cl_count = (int64_t*)malloc(sizeof(int64_t) * k);
     int64_t ncl = 0;
-    for (int j = 0; j < k; ++j) {
+    for (int t = 0; t < k; ++t) {
+      member[t] = ord[t].pos;
       int join = 0;
-      if (j > 0 && ncl > 0) {
-        const eig_t* p = &sel[cl_first[ncl - 1] + cl_count[ncl - 1] - 1];
-        /* join only with the last member if it is the same block and
-           adjacent in that block's order */
-        if (p->block == sel[j].block && p->local + 1 == sel[j].local &&
-            sel[j].value - p->value <= orfac * tnorm)
-          join = 1;
+      if (t > 0) {
+        const eig_t* p = &sel[ord[t - 1].pos];
+        const eig_t* q = &sel[ord[t].pos];
+        join = p->block == q->block && p->local + 1 == q->local && q->value - p->value <= orfac * bnorm[q->block];
       }
       if (join) {
         cl_count[ncl - 1]++;
       } else {
-        cl_first[ncl] = j;
+        cl_first[ncl] = t;
         cl_count[ncl] = 1;
         ++ncl;
       }
     }
-    /* With several blocks, eigenvalues of one block are not contiguous in
-       output order; clusters then only join block-adjacent members, which is
-       what the join test above does (a member of another block in between
-       closes the run). */
-    vec_ctx vc = {d, es, starts, sel, cl_first, cl_count, tnorm, Z, ldz, n};
+    vec_ctx vc = {d, es, starts, sel, member, cl_first, cl_count, bnorm, Z, ldz, n};
     parallel_for(nthreads, ncl, 1, vec_task, &vc);
+    free(bnorm);
+    free(ord);
+    free(member);
     free(cl_first);
     free(cl_count);
   }

@@ -16,7 +16,10 @@ Paper passages (Petschow, Peise, Bientinesi, arXiv:1205.2107):
     (Sec. 2.3, Eqs. Tresnorm and Torthogo);
   * splitting threshold eps*||T|| (Sec. 3.1.1, footnote);
   * bisection and inverse iteration (Sec. 2.1 "BI"; Sec. 3.1, the inverse
-    iteration equation), orfac = 1e-3 (Sec. 2.1 footnote).
+    iteration equation), orfac = 1e-3 (Sec. 2.1 footnote), relative to each
+    split block's norm;
+  * every call first scales T by the power of two that brings G(T) into
+    [1, 2) and scales the eigenvalues back (exact; see _scale_exponent).
 
 The gradient (``adjoint``) is not in the paper: it is the standard first-order
 perturbation of a symmetric eigen-decomposition, written out densely:
@@ -101,6 +104,32 @@ def _offdiag(d: np.ndarray, e) -> np.ndarray:
     return buf
 
 
+def _scale_exponent(d: np.ndarray, e: np.ndarray) -> int:
+    """k such that 2^k G(T) lies in [1, 2) (0 when G(T) is 0 or not finite).
+
+    Reading of the norm and scaling step (Sec. 3.1.1 takes the norm of T; the
+    paper is silent on scaling): the oracle solves 2^k T and divides the
+    eigenvalues by 2^k.  Scaling by a power of two is exact, leaves the
+    eigenvectors unchanged, and keeps every e_i^2 of the Sturm recurrence in
+    the normal range, which fails for T with entries below about 1e-154 (the
+    squares underflow and the counts go wrong) or above about 1e154.
+    """
+    g = float(_load().oracle_gershgorin_norm(d.shape[0], _ptr(d), _ptr(e)))
+    if g == 0.0 or not np.isfinite(g):
+        return 0
+    return 1 - int(np.frexp(g)[1])
+
+
+def _normalised(d, e):
+    """(2^k d, 2^k e padded to n-1 (at least 1), k) for the k of _scale_exponent."""
+    d = _f64(d)
+    eb = _offdiag(d, e)
+    k = _scale_exponent(d, eb)
+    if k == 0:
+        return d, eb, 0
+    return np.ldexp(d, k), np.ldexp(eb, k), k
+
+
 def num_threads(nthreads: int = 0) -> int:
     """Threads the oracle uses for ``nthreads`` (0 = all online cores)."""
     return int(_load().oracle_num_threads(int(nthreads)))
@@ -126,60 +155,59 @@ def split(d, e):
 
 def sturm_count(d, e, x: float) -> int:
     """Number of eigenvalues of the split T strictly below x (Sturm count on T)."""
-    d = _f64(d)
-    return int(_load().oracle_sturm_count(d.shape[0], _ptr(d), _ptr(_offdiag(d, e)), float(x)))
+    d, eb, k = _normalised(d, e)
+    return int(_load().oracle_sturm_count(d.shape[0], _ptr(d), _ptr(eb), float(np.ldexp(float(x), k))))
 
 
 def kth_eigenvalue(d, e, k: int) -> float:
     """lambda_k (1-based, ascending) of the split T by bisection to full accuracy."""
-    d = _f64(d)
+    d, eb, s = _normalised(d, e)
     n = d.shape[0]
     if not 1 <= k <= n:
         raise ValueError("k out of range")
-    return float(_load().oracle_kth_eigenvalue(n, _ptr(d), _ptr(_offdiag(d, e)), int(k)))
+    return float(np.ldexp(_load().oracle_kth_eigenvalue(n, _ptr(d), _ptr(eb), int(k)), -s))
 
 
 def eigvalsh_tridiagonal(d, e, il: int | None = None, iu: int | None = None,
                          nthreads: int = 0) -> np.ndarray:
     """Eigenvalues il..iu (1-based inclusive; default all), ascending."""
-    d = _f64(d)
+    d, eb, s = _normalised(d, e)
     n = d.shape[0]
     il = 1 if il is None else int(il)
     iu = n if iu is None else int(iu)
     k = max(iu - il + 1, 0)
     W = np.zeros(max(k, 1), dtype=np.float64)
-    rc = _load().oracle_eigh(n, _ptr(d), _ptr(_offdiag(d, e)), il, iu, 0.0, int(nthreads),
-                             _ptr(W), None, 0)
+    rc = _load().oracle_eigh(n, _ptr(d), _ptr(eb), il, iu, 0.0, int(nthreads), _ptr(W), None, 0)
     if rc != 0:
         raise ValueError("bad arguments")
-    return W[:k]
+    return np.ldexp(W[:k], -s)
 
 
 def eigh_tridiagonal(d, e, il: int | None = None, iu: int | None = None,
                      orfac: float = 1e-3, nthreads: int = 0):
     """Eigenpairs il..iu: (W[k], Z[n, k]) with orthonormal columns of Z."""
-    d = _f64(d)
+    d, eb, s = _normalised(d, e)
     n = d.shape[0]
     il = 1 if il is None else int(il)
     iu = n if iu is None else int(iu)
     k = max(iu - il + 1, 0)
     W = np.zeros(max(k, 1), dtype=np.float64)
     Zf = np.zeros((max(k, 1), max(n, 1)), dtype=np.float64)  # row j = column j of Z
-    rc = _load().oracle_eigh(n, _ptr(d), _ptr(_offdiag(d, e)), il, iu, float(orfac),
+    rc = _load().oracle_eigh(n, _ptr(d), _ptr(eb), il, iu, float(orfac),
                              int(nthreads), _ptr(W), _ptr(Zf), max(n, 1))
     if rc != 0:
         raise ValueError("bad arguments")
-    return W[:k], Zf[:k, :n].T.copy()
+    return np.ldexp(W[:k], -s), Zf[:k, :n].T.copy()
 
 
 def cluster_vectors(d, e, mus) -> np.ndarray:
     """Inverse-iteration vectors (with Gram-Schmidt) for the given close values."""
-    d = _f64(d)
+    d, eb, s = _normalised(d, e)
     n = d.shape[0]
-    mus = _f64(mus)
+    mus = np.ldexp(_f64(mus), s)
     c = mus.shape[0]
     Zf = np.zeros((c, n), dtype=np.float64)
-    rc = _load().oracle_cluster_vectors(n, _ptr(d), _ptr(_offdiag(d, e)), c, _ptr(mus), _ptr(Zf))
+    rc = _load().oracle_cluster_vectors(n, _ptr(d), _ptr(eb), c, _ptr(mus), _ptr(Zf))
     if rc != 0:
         raise ValueError("bad arguments")
     return Zf.T.copy()
@@ -187,14 +215,14 @@ def cluster_vectors(d, e, mus) -> np.ndarray:
 
 def jacobi(d, e):
     """Dense cyclic Jacobi on the (unsplit) T, n <= 512: (W ascending, V)."""
-    d = _f64(d)
+    d, eb, s = _normalised(d, e)
     n = d.shape[0]
     W = np.zeros(n, dtype=np.float64)
     V = np.zeros((n, n), dtype=np.float64)  # filled column-major
-    rc = _load().oracle_jacobi(n, _ptr(d), _ptr(_offdiag(d, e)), _ptr(W), _ptr(V))
+    rc = _load().oracle_jacobi(n, _ptr(d), _ptr(eb), _ptr(W), _ptr(V))
     if rc != 0:
         raise ValueError("jacobi: n must be in 1..512")
-    return W, V.T.copy()
+    return np.ldexp(W, -s), V.T.copy()
 
 
 def tridiag_dense(d, e) -> np.ndarray:

@@ -173,6 +173,46 @@ def test_split_subset_with_ties_across_blocks():
     check_pairs(d, e, W, Z)
 
 
+def test_cluster_members_separated_by_another_block():
+    """A cluster of one block stays one cluster (re-orthogonalised together)
+    when an eigenvalue of another block lies between its members in
+    ascending order: the pair of W21+ near 9.2107 (gap 5.6e-11) with a 1x1
+    block at its midpoint.  Inverse iteration alone leaves that pair about
+    1e-7 from orthogonal."""
+    d0, e0 = inputs.wilkinson_plus(21)
+    W0 = np.linalg.eigvalsh(oracle.tridiag_dense(d0, e0))
+    lo, hi = W0[17], W0[18]
+    assert 0 < hi - lo < 1e-10
+    d = np.append(d0, lo + (hi - lo) / 2)
+    e = np.append(e0, 0.0)
+    W, Z = oracle.eigh_tridiagonal(d, e)
+    assert W[17] < W[18] < W[19] and W[18] == d[-1]
+    check_pairs(d, e, W, Z, np.sort(np.append(W0, d[-1])))
+
+
+@pytest.mark.parametrize("k", [-1000, -600, 600, 900])
+def test_power_of_two_scaling_is_exact(k):
+    """Eigenpairs of 2^k T are 2^k times those of T bit for bit (the oracle
+    normalises ||T|| by an exact power of two), also where e_i^2 alone would
+    underflow or overflow."""
+    d, e = inputs.wilkinson_plus(21)
+    W, Z = oracle.eigh_tridiagonal(d, e)
+    Ws, Zs = oracle.eigh_tridiagonal(np.ldexp(d, k), np.ldexp(e, k))
+    assert np.array_equal(Ws, np.ldexp(W, k)) and np.array_equal(Zs, Z)
+    assert oracle.sturm_count(np.ldexp(d, k), np.ldexp(e, k), np.ldexp(W[10], k) * (1 + 1e-12)) == 11
+
+
+def test_tiny_block_beside_a_normal_one():
+    """A 1x1 block of magnitude 1e-239 next to a block of norm 1: its
+    inverse iteration runs on the block scaled to norm 1, so the vector is a
+    finite unit vector."""
+    d = np.array([1.0, 2.23341364e-239, 0.0])
+    e = np.array([0.0, 0.0])
+    W, Z = oracle.eigh_tridiagonal(d, e)
+    assert W.tolist() == [0.0, 2.23341364e-239, 1.0]
+    assert np.array_equal(np.abs(Z), np.eye(3)[:, [2, 1, 0]])
+
+
 @pytest.mark.parametrize("maker", [lambda: inputs.wilkinson_plus(201), lambda: inputs.glued_wilkinson(20),
                                    lambda: inputs.uniform(800, 1205), lambda: inputs.toeplitz(800)])
 def test_clustered_vectors(maker):
