@@ -212,6 +212,13 @@ class BatchLayout:
         self.batch = len(sizes)
         il = [1] * self.batch if il is None else [int(x) for x in il]
         iu = list(sizes) if iu is None else [int(x) for x in iu]
+        if any(n < 0 for n in sizes):
+            raise ValueError("problem sizes must be >= 0")
+        if len(il) != self.batch or len(iu) != self.batch:
+            raise ValueError("il and iu need one entry per problem")
+        for p, (n, lo, hi) in enumerate(zip(sizes, il, iu)):
+            if n > 0 and not 1 <= lo <= hi <= n:
+                raise ValueError(f"problem {p}: need 1 <= il <= iu <= n (n={n}, il={lo}, iu={hi})")
         self.ks = [u - l + 1 if n > 0 else 0 for n, l, u in zip(sizes, il, iu)]
         off = [0]
         woff = [0]

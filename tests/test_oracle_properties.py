@@ -132,3 +132,25 @@ def test_vectors_meet_residual_and_orthogonality(T):
     bound = _pair_bounds(d, e, Ws, Z, res)
     bad = np.argwhere(off > bound)
     assert bad.size == 0, f"pairs {bad[:4].tolist()}: {off[tuple(bad[0])]:.3e} > {bound[tuple(bad[0])]:.3e}"
+
+
+@settings(max_examples=100, deadline=None, suppress_health_check=[HealthCheck.too_slow])
+@given(tridiagonals(), st.data())
+def test_subset_is_a_slice_of_the_full_solve(T, data):
+    """Eigenvalues il..iu are exactly the slice of the full solve (the same
+    bisection to full accuracy), and the subset's vectors meet the residual
+    goal and are orthonormal within the subset's own clusters."""
+    d, e = T
+    n = len(d)
+    il = data.draw(st.integers(1, n))
+    iu = data.draw(st.integers(il, n))
+    Wa = oracle.eigvalsh_tridiagonal(d, e)
+    W, Z = oracle.eigh_tridiagonal(d, e, il, iu)
+    assert np.array_equal(W, Wa[il - 1:iu])
+    assert np.array_equal(oracle.eigvalsh_tridiagonal(d, e, il, iu), W)
+    tn = _norm(d, e)
+    k = 1 - int(np.frexp(tn)[1]) if tn > 0 else 0
+    A = oracle.tridiag_dense(np.ldexp(d, k), np.ldexp(e, k))
+    res = np.linalg.norm(A @ Z - Z * np.ldexp(W, k)[None, :], axis=0)
+    assert float(np.max(res)) <= 20 * n * EPS * max(np.ldexp(tn, k), 1.0)
+    assert np.all(np.abs(np.linalg.norm(Z, axis=0) - 1.0) <= 20 * n * EPS)
