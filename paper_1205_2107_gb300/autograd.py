@@ -49,7 +49,7 @@ class EighTridiagonal(torch.autograd.Function):
         ge = torch.zeros(ctx.e_numel, dtype=dbar.dtype, device=dbar.device)
         m = min(ctx.e_numel, max(n - 1, 0))
         ge[:m] = ebar[:m]
-        return dbar, ge, None, None, None
+        return dbar[:n], ge, None, None, None
 
 
 class EighTridiagonalBatched(torch.autograd.Function):
@@ -67,6 +67,7 @@ class EighTridiagonalBatched(torch.autograd.Function):
         ctx.layout = layout
         ctx.tau_rel = float(tau_rel)
         ctx.plan = plan
+        ctx.d_numel = d.numel()
         ctx.e_numel = e.numel()
         ctx.recompute = bool(recompute)
         ctx.save_for_backward(*((d.detach(), e.detach()) if recompute else (W, Z)))
@@ -83,10 +84,14 @@ class EighTridiagonalBatched(torch.autograd.Function):
         Wb = gW.contiguous() if gW is not None else None
         Zb = gZ.contiguous() if gZ is not None else None
         dbar, ebar = api.eigh_tridiagonal_backward(W, Z, Wb, Zb, ctx.layout, tau_rel=ctx.tau_rel, plan=ctx.plan)
+        # d and e may hold more than n_total entries; those get zero gradient
+        nt = ctx.layout.n_total
+        gd = torch.zeros(ctx.d_numel, dtype=dbar.dtype, device=dbar.device)
+        gd[:min(ctx.d_numel, nt)] = dbar[:min(ctx.d_numel, nt)]
         ge = torch.zeros(ctx.e_numel, dtype=dbar.dtype, device=dbar.device)
-        m = min(ctx.e_numel, ebar.numel())
+        m = min(ctx.e_numel, nt)
         ge[:m] = ebar[:m]
-        return dbar, ge, None, None, None, None
+        return gd, ge, None, None, None, None
 
 
 def eigh_tridiagonal_autograd(d: torch.Tensor, e: torch.Tensor, *, tau_rel: float = 0.0, plan=None,
