@@ -109,8 +109,14 @@ class Plan:
         return {"launches": int(prof.launches), "stages": prof.stages()}
 
     def info(self) -> dict:
+        """Synchronise the current stream and return the last solve's status
+        word and counters; raises MrrrError when the synchronisation or the
+        status copy itself fails (ERR_CUDA, which the device never sets as a
+        status: the fields are not written then)."""
         inf = _lib.Info()
-        _lib.load().mrrr_get_status(self._h, _stream_handle(self.device), ctypes.byref(inf))
+        rc = _lib.load().mrrr_get_status(self._h, _stream_handle(self.device), ctypes.byref(inf))
+        if rc == _lib.ERR_CUDA:
+            raise _lib.MrrrError(rc, "mrrr_get_status")
         return inf.as_dict()
 
 

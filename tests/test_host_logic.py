@@ -73,3 +73,86 @@ def test_bench_records_the_host_cpu():
     h = bench.host_cpu()
     assert isinstance(h["model"], str) and h["model"]
     assert h["nproc"] == os.cpu_count() and h["nproc"] >= 1
+
+
+class _FakePlan:
+    """Stands in for api.Plan in the retry loop: records option changes and
+    reports the scripted statuses one solve after another."""
+
+    def __init__(self, statuses):
+        self.statuses = list(statuses)
+        self.options = {}
+        self.solves = 0
+
+    def workspace(self, nbytes):
+        return torch.empty(nbytes, dtype=torch.uint8)
+
+    def info(self):
+        st = self.statuses[min(self.solves, len(self.statuses)) - 1]
+        return {"status": st, "pool_rows_used": 1000 * self.solves, "nodes": 50 * self.solves}
+
+    def set_options(self, **options):
+        self.options.update(options)
+
+
+class _FakeCall:
+    def __init__(self, plan):
+        self.plan = plan
+
+    def ws_bytes(self):
+        return 64
+
+    def __call__(self, ws, nbytes):
+        self.plan.solves += 1
+        return 0
+
+
+def test_retry_grows_capacities_on_a_full_queue():
+    from paper_1205_2107_gb300 import _lib, api
+    plan = _FakePlan([_lib.ERR_QUEUE, _lib.OK])
+    info = api._run_with_retry(plan, _FakeCall(plan), "solve", check=True)
+    assert info["status"] == _lib.OK and plan.solves == 2
+    # grown from what the failed solve reported: twice the rows + 1024, twice the nodes
+    assert plan.options == {"pool_rows": 2 * 1000 + 1024, "max_nodes": 2 * 50}
+
+
+def test_retry_gives_up_and_other_errors_raise_at_once():
+    from paper_1205_2107_gb300 import _lib, api
+    plan = _FakePlan([_lib.ERR_QUEUE] * 10)
+    with pytest.raises(_lib.MrrrError) as ei:
+        api._run_with_retry(plan, _FakeCall(plan), "solve", check=True)
+    assert ei.value.code == _lib.ERR_QUEUE and plan.solves == 4
+    plan = _FakePlan([_lib.ERR_NONFINITE])
+    with pytest.raises(_lib.MrrrError) as ei:
+        api._run_with_retry(plan, _FakeCall(plan), "solve", check=True)
+    assert ei.value.code == _lib.ERR_NONFINITE and plan.solves == 1
+    # unchecked: one solve, no status read
+    plan = _FakePlan([_lib.ERR_QUEUE])
+    assert api._run_with_retry(plan, _FakeCall(plan), "solve", check=False) is None and plan.solves == 1
+
+
+def test_info_raises_when_the_status_read_fails(monkeypatch):
+    """A failed synchronisation or status copy (ERR_CUDA from the host side)
+    must not read as an OK solve; a device status, ERR_ARG included, is
+    returned in the fields."""
+    from paper_1205_2107_gb300 import _lib, api
+
+    class FakeLib:
+        def __init__(self, rc, status):
+            self.rc, self.status = rc, status
+
+        def mrrr_get_status(self, h, stream, out):
+            if self.rc != _lib.ERR_CUDA:
+                out._obj.status = self.status
+            return self.rc
+
+    plan = api.Plan.__new__(api.Plan)
+    plan._h, plan.device = None, torch.device("cpu")
+    monkeypatch.setattr(api, "_stream_handle", lambda dev: None)
+    monkeypatch.setattr(_lib, "load", lambda *a, **k: FakeLib(_lib.ERR_CUDA, 0))
+    with pytest.raises(_lib.MrrrError) as ei:
+        plan.info()
+    assert ei.value.code == _lib.ERR_CUDA
+    monkeypatch.setattr(_lib, "load", lambda *a, **k: FakeLib(_lib.ERR_ARG, _lib.ERR_ARG))
+    assert plan.info()["status"] == _lib.ERR_ARG
+    plan._h = None  # nothing for __del__ to destroy
