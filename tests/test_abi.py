@@ -60,3 +60,37 @@ def test_null_plan_is_rejected(lib):
     assert lib.mrrr_stein(None, 10, None, None, 1, 10, None, None, 10, None, 0, None) == _lib.ERR_ARG
     assert lib.mrrr_plan_destroy(None) == _lib.ERR_ARG
     assert lib.mrrr_plan_create(None, None) == _lib.ERR_ARG
+
+
+def test_every_entry_rejects_a_null_plan_before_any_device_work(lib):
+    """Host-side argument checks return before any CUDA call, so they run
+    here without a GPU."""
+    ERR = _lib.ERR_ARG
+    sz = ctypes.c_size_t()
+    assert lib.mrrr_stein_batched(None, 1, None, None, None, None, None, None, None, None, None, 1, 1, 1, None, 0,
+                                  None) == ERR
+    assert lib.mrrr_autotune_batched(None, 1, None, None, None, None, None, None, None, None, None, 1, 1, 1, None, 0,
+                                     None, None) == ERR
+    assert lib.mrrr_backward(None, 1, None, None, None, None, None, 0.0, 1, 1, None, None, None, 0, None) == ERR
+    assert lib.mrrr_backward_workspace_size(None, 1, 1, ctypes.byref(sz)) == ERR
+    assert lib.mrrr_get_status(None, None, None) == ERR
+    assert lib.mrrr_set_timing(None, 1) == ERR
+    assert lib.mrrr_get_profile(None, None) == ERR
+
+
+def test_static_entry_checks_its_arguments_first(lib):
+    """mrrr_eigenvalues_static: 0 <= n <= MRRR_STATIC_MAX_N, 1 <= il <= iu <=
+    n and non-null pointers, all checked before the scratch is touched."""
+    text = open(os.path.join(ROOT, "include", "mrrr.h")).read()
+    nmax = int(re.search(r"#define MRRR_STATIC_MAX_N (\d+)", text).group(1))
+    buf = (ctypes.c_double * 8)()
+    p = ctypes.cast(buf, ctypes.c_void_p)
+    assert lib.mrrr_eigenvalues_static(0, None, None, 1, 0, None, None) == _lib.OK  # n = 0: no-op
+    assert lib.mrrr_eigenvalues_static(-1, p, p, 1, 1, p, None) == _lib.ERR_ARG
+    assert lib.mrrr_eigenvalues_static(nmax + 1, p, p, 1, 1, p, None) == _lib.ERR_ARG
+    assert lib.mrrr_eigenvalues_static(5, None, p, 1, 5, p, None) == _lib.ERR_ARG
+    assert lib.mrrr_eigenvalues_static(5, p, None, 1, 5, p, None) == _lib.ERR_ARG
+    assert lib.mrrr_eigenvalues_static(5, p, p, 1, 5, None, None) == _lib.ERR_ARG
+    assert lib.mrrr_eigenvalues_static(5, p, p, 0, 3, p, None) == _lib.ERR_ARG
+    assert lib.mrrr_eigenvalues_static(5, p, p, 4, 3, p, None) == _lib.ERR_ARG
+    assert lib.mrrr_eigenvalues_static(5, p, p, 2, 6, p, None) == _lib.ERR_ARG
