@@ -94,3 +94,42 @@ def test_static_entry_checks_its_arguments_first(lib):
     assert lib.mrrr_eigenvalues_static(5, p, p, 0, 3, p, None) == _lib.ERR_ARG
     assert lib.mrrr_eigenvalues_static(5, p, p, 4, 3, p, None) == _lib.ERR_ARG
     assert lib.mrrr_eigenvalues_static(5, p, p, 2, 6, p, None) == _lib.ERR_ARG
+
+
+C_CLIENT = r"""
+#include <stdio.h>
+#include <string.h>
+#include "mrrr.h"
+
+int main(void) {
+  mrrr_options o;
+  if (mrrr_options_default(&o) != MRRR_OK) return 1;
+  if (o.gap_tol != 1e-4 || o.max_depth != 64) return 2;
+  if (mrrr_options_default(NULL) != MRRR_ERR_ARG) return 3;
+  if (strcmp(mrrr_status_string(MRRR_ERR_QUEUE), mrrr_status_string(MRRR_OK)) == 0) return 4;
+  size_t bytes = 0;
+  if (mrrr_workspace_size(NULL, 1, 10, 10, 10, &bytes) != MRRR_ERR_ARG) return 5;
+  if (mrrr_stein(NULL, 10, NULL, NULL, 1, 10, NULL, NULL, 10, NULL, 0, NULL) != MRRR_ERR_ARG) return 6;
+  printf("version %d\n", mrrr_version());
+  return 0;
+}
+"""
+
+
+def test_plain_c_client_links_and_runs(lib, tmp_path):
+    """The header is a C ABI: a C99 program includes it, links libmrrr.so
+    and calls the entry points that need no GPU."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "client.c"
+    src.write_text(C_CLIENT)
+    exe = tmp_path / "client"
+    libdir = os.path.dirname(build.LIB)
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                    str(exe), "-L", libdir, "-l:" + os.path.basename(build.LIB), "-Wl,-rpath," + libdir],
+                   check=True, capture_output=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert out.returncode == 0, (out.returncode, out.stderr)
+    assert out.stdout.strip() == f"version {lib.mrrr_version()}"
