@@ -6,7 +6,8 @@
  * Bientinesi, "High-performance solvers for dense Hermitian eigenproblems"
  * (arXiv:1205.2107), Sec. 3.1.1 "The MRRR algorithm": a root representation
  * L0 D0 L0^T = T - sigma I, bisection for eigenvalue approximations,
- * classification into singletons and clusters by relative gap (tol 1e-3),
+ * classification into singletons and clusters by relative gap (the paper's
+ * tol is 1e-3; here max(gap_tol, 1/m), see mrrr_options.gap_tol),
  * child representations Lc Dc Lc^T = L0 D0 L0^T - sigma_c I for clusters,
  * recursion, and the vector of each singleton from a single solve with a
  * twisted factorization (Eq. errorangle).  The problem statement -- all or an
