@@ -154,3 +154,24 @@ def test_subset_is_a_slice_of_the_full_solve(T, data):
     res = np.linalg.norm(A @ Z - Z * np.ldexp(W, k)[None, :], axis=0)
     assert float(np.max(res)) <= 20 * n * EPS * max(np.ldexp(tn, k), 1.0)
     assert np.all(np.abs(np.linalg.norm(Z, axis=0) - 1.0) <= 20 * n * EPS)
+
+
+@settings(max_examples=200, deadline=None)
+@given(tridiagonals())
+def test_gershgorin_norm_and_split_rule(T):
+    """G(T) is the largest absolute row sum of the dense T (the infinity
+    norm), and the split zeroes exactly the e_i with |e_i| <= eps G(T)
+    (Sec. 3.1.1, footnote on numerical irreducibility), starting a block
+    after each."""
+    d, e = T
+    n = len(d)
+    A = oracle.tridiag_dense(d, e)
+    g = oracle.gershgorin_norm(d, e)
+    if n:
+        with np.errstate(over="ignore"):
+            rows = np.sum(np.abs(A), axis=1)
+        assert g == np.max(rows) or np.isclose(g, np.max(rows), rtol=4 * EPS, atol=0)
+    es, starts = oracle.split(d, e)
+    cut = np.abs(e) <= EPS * g
+    assert np.array_equal(es, np.where(cut, 0.0, e))
+    assert starts.tolist() == [0] + [i + 1 for i in np.flatnonzero(cut)] + [n]
