@@ -175,3 +175,22 @@ def test_gershgorin_norm_and_split_rule(T):
     cut = np.abs(e) <= EPS * g
     assert np.array_equal(es, np.where(cut, 0.0, e))
     assert starts.tolist() == [0] + [i + 1 for i in np.flatnonzero(cut)] + [n]
+
+
+@settings(max_examples=100, deadline=None, suppress_health_check=[HealthCheck.too_slow])
+@given(tridiagonals())
+def test_jacobi_matches_lapack(T):
+    """The dense cyclic Jacobi solver (brute force for small n) on the same
+    structured inputs: eigenvalues within 4 n eps ||T|| of LAPACK's,
+    orthonormal vectors, residual within 20 n eps ||T||."""
+    d, e = T
+    n = len(d)
+    W, V = oracle.jacobi(d, e)
+    Wl = scipy.linalg.eigvalsh_tridiagonal(d, e) if n > 1 else d.copy()
+    tn = max(float(np.max(np.abs(Wl))), np.finfo(float).tiny)
+    assert np.max(np.abs(np.sort(W) - Wl)) <= 4 * n * EPS * tn
+    assert float(np.max(np.abs(V.T @ V - np.eye(n)))) <= 20 * n * EPS
+    k = 1 - int(np.frexp(tn)[1])
+    A = oracle.tridiag_dense(np.ldexp(d, k), np.ldexp(e, k))
+    R = A @ V - V * np.ldexp(W, k)[None, :]
+    assert float(np.max(np.linalg.norm(R, axis=0))) <= 20 * n * EPS * 2.0
