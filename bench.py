@@ -33,14 +33,17 @@ from paper_1205_2107_gb300 import inputs  # noqa: E402
 METRIC = "FP64 tridiagonal eigenpairs/s + roofline fraction; batched & adjoint vs plain"
 UNIT = "eigenpairs/s"
 WORKLOAD = "clustered spectra n~20000: Wilkinson W+ n=20001 + glued W21+ x952 (n=19992, glue 1e-10), all eigenpairs"
+# FP64 peaks are measured on the GPU at run time (mrrr_probe_peak); these
+# derived figures are used only when no GPU probe ran
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070  # SMs x DFMA/clk/SM x flops/DFMA x GHz (max SM clock)
+PEAKS = {"dfma": FP64_PEAK_GFLOPS * 1e9, "dmma": None, "ddiv": None, "source": "derived"}
 # Fixed algorithmic model per eigenpair and matrix row: bisection 4 flops per
 # Sturm step with B = 32 steps, plus 15 flops for the twisted factorization,
 # solve and normalisation; 8 bytes of Z written.
 BISECT_FLOPS_PER_ROW = 4 * 32
 PATH_FLOPS_PER_ROW = BISECT_FLOPS_PER_ROW + 15
 ENGINE_STAGES = ("bisect_root", "prerefine", "refine", "final_bisect")
-DIV_COST_DFMA = 9.0  # measured: DFMA 602 G/s, DDIV 67 G/s on this part
+DIV_COST_DFMA = 9.0  # DFMA-equivalents of one FP64 division; replaced by the measured ratio
 ENGINE_BYTES_PER_CHILD_ROW = 32  # engine DRAM traffic per child-representation row (ncu, W+ n=2001)
 
 
@@ -266,6 +269,11 @@ def run_ours(args, rank: int, world: int):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     build.build()
+    # the roofline denominators, measured on this GPU before anything else runs
+    global FP64_PEAK_GFLOPS, DIV_COST_DFMA
+    PEAKS.update({k: api.probe_peak(k) for k in ("dfma", "dmma", "ddiv")}, source="measured")
+    FP64_PEAK_GFLOPS = PEAKS["dfma"] / 1e9
+    DIV_COST_DFMA = PEAKS["dfma"] / 2.0 / PEAKS["ddiv"]
     mats = workload_matrices()
     sizes = [len(d) for _, d, _ in mats]
     pairs_per_step = sum(sizes)
@@ -273,7 +281,9 @@ def run_ours(args, rank: int, world: int):
     lay = api.BatchLayout(sizes, dev)
     d_cat = torch.tensor(np.concatenate([d for _, d, _ in mats]), device=dev)
     e_cat = torch.tensor(np.concatenate([np.append(e, 0.0) for _, _, e in mats]), device=dev)
-    plan = api.Plan(local)
+    # the timed step: one CUDA graph replay per step (setup, the cluster
+    # levels in a conditional while node decided on the device, the vectors)
+    plan = api.Plan(local, use_graph=1)
     plans = [plan]
     W_out = torch.empty(lay.k_total, dtype=torch.float64, device=dev)
     Z_out = torch.empty(lay.z_total, dtype=torch.float64, device=dev)
@@ -288,8 +298,22 @@ def run_ours(args, rank: int, world: int):
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    for _ in range(max(args.warmup, 3) if args.warmup > 0 else 0):
+    # the first warm-up step is verified against the accuracy goals: a
+    # solution that misses them stops the benchmark instead of being timed
+    verified = None
+    for w in range(max(args.warmup, 3) if args.warmup > 0 else 0):
         step(check=True)
+        if w == 0:
+            verified = {}
+            Ws_, Zs_ = lay.unpack(W_out, Z_out)
+            for p, (name, _, _) in enumerate(mats):
+                a, b = lay.offsets_host[p], lay.offsets_host[p + 1]
+                verified[name] = verify_solution(d_cat[a:b], e_cat[a:b], Ws_[p], Zs_[p], seed=p)
+                bad = [k for k, x in verified[name].items() if (x is False) or (not isinstance(x, bool) and x > 1.0)]
+                if bad:
+                    raise SystemExit(f"{name}: solution misses the accuracy goals ({bad}): {verified[name]}")
+            del Ws_, Zs_
+            torch.cuda.empty_cache()
     for plan in plans:
         plan.set_timing(True)
     barrier()
@@ -314,14 +338,46 @@ def run_ours(args, rank: int, world: int):
                     stage_ms[k] = stage_ms.get(k, 0.0) + v
     barrier()
     child_rows = 0
+    safeguards = {}
+    engine_work = {}
     for plan in plans:
         info = plan.info()
         if info["status"] != 0:
             raise SystemExit(f"solver reported status {info['status']} ({info})")
         plan.set_timing(False)
         child_rows += int(info["pool_rows_used"]) - sum(sizes)
+        # how often the method's safeguards fired in the last timed solve
+        safeguards = {"fallbacks": info["fallbacks"], "child_growth_bound_missed": info["diag"][5],
+                      "child_second_wave": info["diag"][4], "child_recomputed": info["diag"][9],
+                      "orthogonality_fix_runs": info["diag"][8], "depth": info["depth"], "levels": info["levels"],
+                      "cluster_nodes": info["nodes"], "twisted_solves": info["twisted_solves"]}
+        # the interval engine's actual work, per mode: Sturm counts per
+        # eigenpair (the fixed model counts 32) and the share of warp lanes
+        # that counted (a warp pass costs its FP64 instructions either way)
+        modes = ("root", "cluster_ends", "cluster_members", "singletons")
+        engine_work = {
+            "counts_per_eigenpair": {m: info["sturm_counts"][i] / pairs_per_step for i, m in enumerate(modes)},
+            "counts_per_eigenpair_total": sum(info["sturm_counts"]) / pairs_per_step,
+            "lane_utilisation": {m: info["sturm_counts"][i] / max(32 * info["warp_passes"][i], 1)
+                                 for i, m in enumerate(modes)},
+            "warp_pass_rows": sum(r // max(c, 1) * p for r, c, p in zip(info["sturm_rows"], info["sturm_counts"],
+                                                                        info["warp_passes"])),
+        }
     total_ms = max_over_ranks(sum(times), world, dev)
     value = whole_job_rate(pairs_per_step, args.steps, total_ms, world)
+
+    # cross-check of the stage split outside the timed region: one direct-
+    # launch solve (host reads the level count) with CUDA events between the
+    # stages on the solve stream
+    dplan = api.Plan(local)
+    api.eigh_tridiagonal_batched(d_cat, e_cat, lay, plan=dplan, out=(W_out, Z_out))
+    dplan.set_timing(True)
+    flush.zero_()
+    torch.cuda.synchronize(dev)
+    api.eigh_tridiagonal_batched(d_cat, e_cat, lay, plan=dplan, out=(W_out, Z_out), check=False)
+    torch.cuda.synchronize(dev)
+    stages_direct = dplan.profile()["stages"]
+    del dplan
 
     # the same two matrices solved one after the other by the single-problem
     # path (for comparison only)
@@ -381,7 +437,7 @@ def run_ours(args, rank: int, world: int):
                                   "6 engine launches = 31 bytes per child-representation row: refine and final "
                                   "each read every child row once) by the step's child rows",
                 "engine_ms_per_step": engine_ms,
-                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz (max SM clock)"}
+                "peak_source": "measured on this GPU by mrrr_probe_peak (FP64 FMA throughput, all SMs)"}
     # whole path against T_roof = max(F / P_fp64, 8 n k / BW), F = 143 n k
     t_flop = PATH_FLOPS_PER_ROW * nk / (FP64_PEAK_GFLOPS * 1e9)
     t_hbm = 8.0 * nk / (HBM_GBS * 1e9)
@@ -402,25 +458,76 @@ def run_ours(args, rank: int, world: int):
         cpu = {"value": p / t, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": sample_text(windows, len(mats), cores, t), "host": host_cpu()}
     side = None
+    large = None
     if not args.no_side:
         side = side_by_side(args, dev, flush)
+        large = large_legs(dev, flush)
     clocks = clk.summary()
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": sizes, "eigenpairs_per_step": pairs_per_step,
-                       "schedule": "both matrices in one batched solve (mrrr_stein_batched)",
+                       "schedule": "both matrices in one batched solve (mrrr_stein_batched), one CUDA graph "
+                                   "replay per step: cluster levels in a conditional while node",
                        "sequential_plain_ms": t_seq,
+                       "verified": verified,
                        "l2": "flushed before each step (256 MB write); Z output 3.2 GB per matrix",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            "clocks": clocks, "gpu_launches": launches,
+            "clocks": clocks, "gpu_launches": launches, "safeguards": safeguards, "engine_work": engine_work,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": [round(1e3 * t, 1) for t in e2e_times], "clocks": clk_e2e.summary()},
             "roofline": roof, "path_roofline": path_roof, "cpu_baseline": cpu,
+            "peaks": {"fp64_fma_gflops": PEAKS["dfma"] / 1e9,
+                      "fp64_mma_gflops": PEAKS["dmma"] / 1e9 if PEAKS["dmma"] else None,
+                      "fp64_div_g_per_s": PEAKS["ddiv"] / 1e9 if PEAKS["ddiv"] else None,
+                      "source": PEAKS["source"]},
             "batched": side["batched"] if side else None, "adjoint": side["adjoint"] if side else None,
-            "stages_ms_per_step": {k: v / args.steps for k, v in sorted(stage_ms.items())}}
+            "large_n50000": large,
+            "stages_ms_per_step": {k: v / args.steps for k, v in sorted(stage_ms.items())},
+            "stages_source": "timed graph replays: GPU global timer read by one-thread kernels at the stage "
+                             "boundaries inside the graph, summed over the steps",
+            "stages_ms_direct_launch": stages_direct}
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def verify_solution(d, e, W, Z, seed: int = 0) -> dict:
+    """Accuracy of one solved problem against the goals (Sec. 2.3, Eqs.
+    Tresnorm and Torthogo), from properties that hold at any size, computed
+    on the GPU: W ascending, every residual ||T z - lambda z|| <= 20 n eps ||T||,
+    |Z^T Z - I| <= 20 n eps over all columns against 1,024 seeded columns and
+    over each column's 256 neighbours on each side, and the trace identity
+    sum lambda = sum d within n * 4 n eps ||T||.  ||T|| = max|lambda|.
+    Returns the worst ratios to the bounds (<= 1 passes)."""
+    import torch
+    eps = 2.0 ** -53
+    n = d.numel()
+    tn = float(W.abs().max())
+    asc = bool((W[1:] >= W[:-1]).all()) if n > 1 else True
+    res = 0.0
+    for a in range(0, n, 4096):
+        Zc = Z[:, a:a + 4096]
+        TZ = d[:, None] * Zc
+        TZ[:-1] += e[:n - 1, None] * Zc[1:]
+        TZ[1:] += e[:n - 1, None] * Zc[:-1]
+        res = max(res, float(torch.linalg.vector_norm(TZ - Zc * W[None, a:a + 4096], dim=0).max()))
+        del TZ
+    cols = torch.as_tensor(np.random.default_rng(seed).choice(n, min(n, 1024), replace=False), device=Z.device)
+    G = Z.t() @ Z[:, cols]
+    G[cols, torch.arange(cols.numel(), device=Z.device)] -= 1.0
+    orth = float(G.abs().max())
+    del G
+    for a in range(0, n, 2048):
+        b = min(n, a + 2048)
+        lo, hi = max(0, a - 256), min(n, b + 256)
+        G = Z[:, a:b].t() @ Z[:, lo:hi]
+        idx = torch.arange(a, b, device=Z.device)
+        G[idx - a, idx - lo] -= 1.0
+        orth = max(orth, float(G.abs().max()))
+        del G
+    trace = abs(float(W.sum()) - float(d.sum()))
+    return {"ascending": asc, "residual": res / (20 * n * eps * tn), "orthogonality": orth / (20 * n * eps),
+            "trace": trace / (4 * n * n * eps * tn)}
 
 
 def _time_cuda(fn, reps: int, flush) -> float:
@@ -437,6 +544,40 @@ def _time_cuda(fn, reps: int, flush) -> float:
         e1.synchronize()
         total += e0.elapsed_time(e1)
     return total / reps
+
+
+def large_legs(dev, flush):
+    """The largest single-GPU configuration: n = 50,000, d iid U[0,1], e iid
+    U[0, 1e-2] (seed 50000; Z = 20 GB in HBM), all eigenpairs and separately
+    the index subset 25001..30000, each timed with CUDA events (mean of two
+    solves after a checked warm-up), against T_roof = max(143 n k / P_fp64,
+    8 n k / BW)."""
+    import torch
+    from paper_1205_2107_gb300 import api
+    d, e = inputs.large_uniform()
+    n = len(d)
+    dt = torch.tensor(d, device=dev)
+    et = torch.tensor(np.append(e, 0.0), device=dev)
+    out = {}
+    for name, il, iu in (("all", 1, n), ("subset_25001_30000", 25001, 30000)):
+        plan = api.Plan(dev, use_graph=1)
+        k = iu - il + 1
+        api.eigh_tridiagonal(dt, et, il, iu, plan=plan)  # checked: sizes the plan's capacities
+        torch.cuda.synchronize()
+
+        def one():
+            api.eigh_tridiagonal(dt, et, il, iu, plan=plan, check=False)
+
+        ms = _time_cuda(one, 2, flush)
+        if plan.info()["status"] != 0:
+            raise SystemExit(f"n=50000 {name}: solver reported an error")
+        nk = n * k
+        t_roof = max(PATH_FLOPS_PER_ROW * nk / (FP64_PEAK_GFLOPS * 1e9), 8.0 * nk / (HBM_GBS * 1e9))
+        out[name] = {"n": n, "il": il, "iu": iu, "eigenpairs": k, "ms": ms, "eigenpairs_per_s": k / (ms * 1e-3),
+                     "path_roofline_frac": 1e3 * t_roof / ms, "timing": "CUDA graph replay, CUDA events"}
+        del plan
+        torch.cuda.empty_cache()
+    return out
 
 
 def side_by_side(args, dev, flush):
@@ -531,10 +672,10 @@ def side_by_side(args, dev, flush):
         "workload": "256 STEPs n=512, d, e iid N(0,1) (seed 1206); loss sum w_i lambda_i + sum (c_i^T z_i)^2",
         "forward_ms": t_f, "backward_ms": t_bw, "backward_over_forward": t_bw / t_f,
         "backward_tflops": flops_bw / (t_bw * 1e-3) / 1e12,
-        "backward_frac_of_fp64_peak": flops_bw / (t_bw * 1e-3) / 1e9 / FP64_PEAK_GFLOPS,
-        "fp64_peak_tflops": FP64_PEAK_GFLOPS / 1e3,
-        "fp64_peak_source": "derived FP64 pipe peak (152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz); "
-                            "the backward GEMMs run on the FP64 MMA (mma.sync m8n8k4 f64)",
+        "backward_frac": flops_bw / (t_bw * 1e-3) / max(PEAKS["dfma"], PEAKS["dmma"] or 0.0),
+        "fp64_peaks_tflops": {"dfma": PEAKS["dfma"] / 1e12,
+                              "dmma": PEAKS["dmma"] / 1e12 if PEAKS["dmma"] else None},
+        "peak_source": "the better of the measured FP64 FMA and FP64 MMA rates (mrrr_probe_peak)",
     }
     return {"batched": batched_line, "adjoint": adjoint_line}
 

@@ -69,12 +69,15 @@ typedef struct mrrr_options {
   int max_bisect_steps;    /* per interval and pass (256) */
   int engine_blocks_per_sm; /* 256-thread CTAs per SM of the interval engine (2; 1 or 2) */
   int threads_per_block;   /* CUDA block size of the interval kernels (128) */
-  int vec_blocks_per_sm;   /* 128-thread blocks per SM of the eigenvector kernel (8);
+  int vec_blocks_per_sm;   /* 128-thread blocks per SM of the eigenvector kernel (4, what
+                              its registers allow to be resident at once);
                               capped by the number of eigenpairs */
-  int use_graph;           /* 1: the solve's launches (levels driven on the device, no host
-                              synchronisation) are captured once into a CUDA graph per call
-                              signature and replayed; 0: launched directly, the host reads
-                              the new-cluster count after each level (default) */
+  int use_graph;           /* 1: the solve is captured once per call signature into a CUDA
+                              graph and replayed: setup, then the cluster levels in a
+                              conditional while node that runs one more level for as long as
+                              the last one made new clusters (decided on the device, no host
+                              synchronisation), then the vectors; 0: launched directly, the
+                              host reads the new-cluster count after each level (default) */
   int64_t max_nodes;       /* capacity of the cluster-node table (0 = automatic) */
   int64_t pool_rows;       /* capacity of the child-representation pool in rows of
                               32 bytes (0 = automatic) */
@@ -86,6 +89,17 @@ typedef struct mrrr_options {
                               at most m/8 for a block of order m; negative = none) */
   double width_scale;      /* scales the resident lanes when the engine chooses its
                               multisection width (1.0; larger = more points per interval) */
+  int multisection_width;  /* 0: the engine picks the points per interval from the length of
+                              its work list, and consecutive eigenvalues of one node whose
+                              brackets coincide pool their points (default); 1..32 (a power
+                              of two): that many points per interval, no pooling -- a fixed
+                              schedule, under which an eigenpair comes out bit for bit the
+                              same whatever else the solve or the batch holds */
+  int root_side;           /* side of the spectrum where the root shift sits: 0 the
+                              Gershgorin end nearer the wanted indices (default), 1 the left
+                              end, 2 the right end (slices of one index range that must share
+                              one root representation) */
+  int reserved_[6];        /* zero */
 } mrrr_options;
 
 /* Counters reported by mrrr_get_status (device values after the last solve). */
@@ -100,11 +114,19 @@ typedef struct mrrr_info {
   int64_t levels;          /* cluster levels processed                      */
   int64_t diag[12];        /* event counters: [0] root-shift retries exhausted,
                               [1] root bisection cap, [2] child bracket not
-                              confirmed, [3] child bisection cap, [4] unused,
+                              confirmed, [3] child bisection cap, [4] clusters
+                              whose first wave of child shifts all failed,
                               [5] child growth bound missed, [6] depth-limit
                               fallbacks, [7] capacity fallbacks, [8] runs of
                               neighbouring eigenvectors re-orthogonalised,
-                              [9]-[11] unused */
+                              [9] child transforms computed again with stores,
+                              [10]-[11] unused */
+  int64_t sturm_counts[4]; /* interval engine per mode (0 root bisection, 1 cluster ends in
+                              the parent, 2 cluster members in the child, 3 singletons to
+                              full accuracy): Sturm counts evaluated */
+  int64_t sturm_rows[4];   /* rows those counts ran over */
+  int64_t warp_passes[4];  /* warp-wide passes over the rows (a pass costs its FP64
+                              instructions however many of the 32 lanes count) */
 } mrrr_info;
 
 typedef struct mrrr_plan mrrr_plan;
@@ -252,8 +274,13 @@ mrrr_status mrrr_backward_workspace_size(const mrrr_plan* plan, int batch, int64
  * Calls whose work overlaps on the GPU (different streams, or different host
  * threads, on the same device) race on the array and give wrong results:
  * serialise them.  The first call on each device looks up the array's device
- * address (cudaGetSymbolAddress, with that device current) and caches it;
- * make that first call before any stream capture.  Device-side errors
+ * address (cudaGetSymbolAddress, with that device current) and caches it for
+ * the life of the process; make that first call before any stream capture.
+ * The cached address belongs to the device's primary context: after
+ * cudaDeviceReset on a device, this entry point must not be called on that
+ * device again in the same process.  The root representation is built by
+ * one thread (a sequential recurrence over n rows), the bisection by one
+ * thread per eigenvalue.  Device-side errors
  * (non-finite input, no definite root shift) give NaN eigenvalues.  Returns
  * MRRR_ERR_ARG for bad host-side arguments and MRRR_ERR_CUDA when the
  * address lookup or a launch fails.
@@ -263,10 +290,13 @@ mrrr_status mrrr_eigenvalues_static(int n, const double* d, const double* e, int
                                     mrrr_stream stream);
 
 /* Stage profile of the last solve on a plan.  launches counts the kernels
-   the solve enqueued; when timing is enabled (mrrr_set_timing) the solve
-   records CUDA events between its stages on its stream and ms[i] holds the
-   time of stage name[i] summed over cluster levels.  Not in the paper:
-   measurement support. */
+   the solve ran.  Direct launches: when timing is enabled (mrrr_set_timing)
+   the solve records CUDA events (a pool created once per plan) between its
+   stages on its stream and ms[i] holds the time of stage name[i] summed over
+   cluster levels.  Graph replays (use_graph): one-thread kernels at the
+   stage boundaries accumulate the GPU global timer's advance per stage in
+   the workspace, read back here (synchronise the stream first).  Not in the
+   paper: measurement support. */
 typedef struct mrrr_profile {
   int64_t launches;
   int nstages;
@@ -281,6 +311,16 @@ mrrr_status mrrr_set_timing(mrrr_plan* plan, int enable);
 
 /* Copy the profile of the last solve on the plan into *out. */
 mrrr_status mrrr_get_profile(const mrrr_plan* plan, mrrr_profile* out);
+
+/* Measured peak rate of one arithmetic unit of the current GPU, the
+   denominator of the solver's roofline figures.  Not in the paper:
+   measurement support.  kind 0: FP64 FMA (flop/s, 2 per FMA), 1: FP64 tensor
+   core MMA m8n8k4 (flop/s), 2: FP64 division (divisions/s), 3: FP32 FMA
+   (flop/s).  Times throughput kernels on every SM with CUDA events on a
+   stream of its own (best of three, about 0.1-0.2 s in all) and
+   synchronises.  Returns MRRR_ERR_ARG for a bad kind or NULL rate,
+   MRRR_ERR_CUDA when a launch fails. */
+mrrr_status mrrr_probe_peak(int kind, double* rate);
 
 /* Synchronise stream and report the device status word and counters of the
    last solve on this plan.  out may be NULL.  Returns info.status. */

@@ -23,7 +23,7 @@ OK, ERR_ARG, ERR_WORKSPACE, ERR_NONFINITE, ERR_NOCONV, ERR_QUEUE, ERR_TIMEOUT, E
 EXPORTS = ["mrrr_options_default", "mrrr_plan_create", "mrrr_plan_destroy", "mrrr_workspace_size",
            "mrrr_stein", "mrrr_stein_batched", "mrrr_backward", "mrrr_backward_workspace_size",
            "mrrr_get_status", "mrrr_status_string", "mrrr_version", "mrrr_set_timing", "mrrr_get_profile",
-           "mrrr_eigenvalues_static", "mrrr_autotune_batched"]
+           "mrrr_eigenvalues_static", "mrrr_autotune_batched", "mrrr_probe_peak"]
 STATIC_MAX_N = 8192  # MRRR_STATIC_MAX_N
 
 
@@ -32,16 +32,20 @@ class Options(ctypes.Structure):
                 ("max_bisect_steps", c_int), ("engine_blocks_per_sm", c_int), ("threads_per_block", c_int),
                 ("vec_blocks_per_sm", c_int), ("use_graph", c_int), ("max_nodes", c_int64),
                 ("pool_rows", c_int64), ("cluster_rtol", c_double), ("root_perturb", c_double),
-                ("width_scale", c_double)]
+                ("width_scale", c_double), ("multisection_width", c_int), ("root_side", c_int),
+                ("reserved_", c_int * 6)]
 
 
 class Info(ctypes.Structure):
     _fields_ = [("status", c_int), ("depth", c_int), ("nodes", c_int64), ("pool_rows_used", c_int64),
-                ("fallbacks", c_int64), ("twisted_solves", c_int64), ("levels", c_int64), ("diag", c_int64 * 12)]
+                ("fallbacks", c_int64), ("twisted_solves", c_int64), ("levels", c_int64), ("diag", c_int64 * 12),
+                ("sturm_counts", c_int64 * 4), ("sturm_rows", c_int64 * 4), ("warp_passes", c_int64 * 4)]
 
     def as_dict(self) -> dict:
-        out = {f: getattr(self, f) for f, _ in self._fields_ if f != "diag"}
-        out["diag"] = list(self.diag)
+        arrays = ("diag", "sturm_counts", "sturm_rows", "warp_passes")
+        out = {f: getattr(self, f) for f, _ in self._fields_ if f not in arrays}
+        for f in arrays:
+            out[f] = list(getattr(self, f))
         return out
 
 
@@ -104,6 +108,7 @@ def load(build_if_missing: bool = False):
         lib.mrrr_eigenvalues_static.argtypes = [c_int, dp, dp, c_int, c_int, dp, P]
         lib.mrrr_autotune_batched.argtypes = [P, c_int, dp, dp, dp, dp, dp, dp, dp, dp, dp, c_int64, c_int64,
                                               c_int, dp, c_size_t, P, ctypes.POINTER(Tuning)]
+        lib.mrrr_probe_peak.argtypes = [c_int, ctypes.POINTER(c_double)]
         for name in EXPORTS:
             if name not in ("mrrr_status_string", "mrrr_version"):
                 getattr(lib, name).restype = c_int

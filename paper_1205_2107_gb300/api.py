@@ -14,6 +14,12 @@ from . import _lib
 
 _F64 = torch.float64
 
+# Default gap threshold of the backward pass, relative to max|W| (the
+# spectral norm of T): eigenvalue pairs closer than 64 eps ||T|| cannot be
+# told apart by any FP64 solver, so their term F(i, j) = 1/(W_j - W_i) is
+# dropped instead of amplifying rounding errors by 1/gap.
+DEFAULT_TAU_REL = 64.0 * 2.0 ** -53
+
 
 def _stream_handle(device: torch.device) -> ctypes.c_void_p:
     return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
@@ -279,7 +285,8 @@ def eigh_tridiagonal_batched(d: torch.Tensor, e: torch.Tensor, layout: BatchLayo
 
 
 def eigh_tridiagonal_backward(W: torch.Tensor, Z: torch.Tensor, Wbar: torch.Tensor | None,
-                              Zbar: torch.Tensor | None, layout: BatchLayout, *, tau_rel: float = 0.0,
+                              Zbar: torch.Tensor | None, layout: BatchLayout, *,
+                              tau_rel: float = DEFAULT_TAU_REL,
                               plan: Plan | None = None, check: bool = True):
     """Gradient (dbar, ebar) of a loss with respect to packed (d, e), given
     the packed all-eigenpair solution (W, Z) of ``layout`` and the loss
@@ -287,7 +294,8 @@ def eigh_tridiagonal_backward(W: torch.Tensor, Z: torch.Tensor, Wbar: torch.Tens
 
     dbar and ebar have the packing of d and e (ebar's last entry of each
     problem is 0).  F(i, j) = 1/(W_j - W_i) is dropped where the gap is at
-    most tau_rel * max|W| of the problem.
+    most tau_rel * max|W| of the problem (default 64 eps: numerically equal
+    eigenvalues, whose individual vectors are not defined).
     """
     if not layout.all:
         raise ValueError("the backward pass needs all eigenpairs of every problem")
@@ -341,3 +349,15 @@ def autotune_batched(d: torch.Tensor, e: torch.Tensor, layout: BatchLayout, *, p
     plan.options.update(engine_blocks_per_sm=int(t.engine_blocks_per_sm), width_scale=float(t.width_scale))
     return {"engine_blocks_per_sm": int(t.engine_blocks_per_sm), "width_scale": float(t.width_scale),
             "best_ms": float(t.best_ms), "default_ms": float(t.default_ms), "configs": int(t.configs)}
+
+
+PEAK_KINDS = {"dfma": 0, "dmma": 1, "ddiv": 2, "ffma": 3}
+
+
+def probe_peak(kind: str) -> float:
+    """Measured peak rate of one unit of the current GPU (mrrr_probe_peak):
+    'dfma' and 'dmma' in FP64 flop/s, 'ddiv' in divisions/s, 'ffma' in FP32
+    flop/s."""
+    rate = ctypes.c_double(0.0)
+    _lib.check(_lib.load().mrrr_probe_peak(PEAK_KINDS[kind], ctypes.byref(rate)), "mrrr_probe_peak")
+    return float(rate.value)

@@ -9,7 +9,9 @@ The gradient follows first-order perturbation theory of T = Z diag(W) Z^T
 (dbar_j = Tbar(j,j), ebar_j = Tbar(j,j+1) + Tbar(j+1,j) for
 Tbar = Z (diag(Wbar) + F o (Z^T Zbar)) Z^T); it is defined for losses that
 do not depend on the signs of the columns of Z, and for separated
-eigenvalues (gaps at most tau_rel * max|W| are dropped from F).
+eigenvalues: gaps at most tau_rel * max|W| are dropped from F (default
+api.DEFAULT_TAU_REL = 64 eps, i.e. pairs closer than 64 eps ||T||, which no
+FP64 solver can tell apart).
 """
 from __future__ import annotations
 
@@ -24,7 +26,7 @@ class EighTridiagonal(torch.autograd.Function):
     deterministic, so W and Z come out identical)."""
 
     @staticmethod
-    def forward(ctx, d, e, tau_rel=0.0, plan=None, recompute=False):
+    def forward(ctx, d, e, tau_rel=api.DEFAULT_TAU_REL, plan=None, recompute=False):
         W, Z = api.eigh_tridiagonal(d.detach(), e.detach(), plan=plan)
         ctx.tau_rel = float(tau_rel)
         ctx.plan = plan
@@ -58,7 +60,7 @@ class EighTridiagonalBatched(torch.autograd.Function):
     keeping Z (sum n_p^2 doubles) alive between the passes."""
 
     @staticmethod
-    def forward(ctx, d, e, layout, tau_rel=0.0, plan=None, recompute=False):
+    def forward(ctx, d, e, layout, tau_rel=api.DEFAULT_TAU_REL, plan=None, recompute=False):
         if not layout.all:
             raise ValueError("autograd needs all eigenpairs of every problem")
         W, Z = api.eigh_tridiagonal_batched(d.detach(), e.detach(), layout, plan=plan)
@@ -94,13 +96,14 @@ class EighTridiagonalBatched(torch.autograd.Function):
         return gd, ge, None, None, None, None
 
 
-def eigh_tridiagonal_autograd(d: torch.Tensor, e: torch.Tensor, *, tau_rel: float = 0.0, plan=None,
-                              recompute: bool = False):
+def eigh_tridiagonal_autograd(d: torch.Tensor, e: torch.Tensor, *, tau_rel: float = api.DEFAULT_TAU_REL,
+                              plan=None, recompute: bool = False):
     """All eigenpairs (W, Z) of one tridiagonal, differentiable in (d, e)."""
     return EighTridiagonal.apply(d, e, tau_rel, plan, recompute)
 
 
-def eigh_tridiagonal_batched_autograd(d: torch.Tensor, e: torch.Tensor, layout, *, tau_rel: float = 0.0,
+def eigh_tridiagonal_batched_autograd(d: torch.Tensor, e: torch.Tensor, layout, *,
+                                      tau_rel: float = api.DEFAULT_TAU_REL,
                                       plan=None, recompute: bool = False):
     """Packed all-eigenpair solution of a batch, differentiable in (d, e);
     recompute trades a second solve for not keeping Z between the passes."""

@@ -44,7 +44,10 @@ struct mrrr_plan {
   cudaGraphExec_t exec;
   GraphKey key;
   bool have_graph;
+  bool graph_conditional;  // the graph runs its levels in a conditional while node
+  bool last_graph;         // the last solve was a graph replay (device-clock stage times)
   int64_t graph_launches;
+  int64_t graph_part_launches[3];  // conditional graph: kernels before, per level, after the loop
 };
 
 namespace mrrr {
@@ -56,6 +59,31 @@ thread_local StageTimer* g_timer = nullptr;
 StageTimer* stage_timer() { return g_timer; }
 void set_stage_timer(StageTimer* t) { g_timer = t; }
 
+const char* const kStageNames[ST_COUNT] = {"prep",     "root",     "bisect_root", "rank",         "classify",
+                                           "prerefine", "childrep", "refine",      "final_bisect", "vectors"};
+
+int stage_index(const char* name) {
+  for (int i = 0; i < ST_COUNT; ++i)
+    if (std::strcmp(kStageNames[i], name) == 0) return i;
+  return -1;
+}
+
+namespace {
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Device-clock stage mark: the time since the previous mark goes to stage id
+// (id < 0: only the reference point is set).
+__global__ void k_stage_mark(Ctl* c, int id) {
+  const unsigned long long t = global_ns();
+  if (id >= 0) c->stage_ns[id] += t - c->t_last;
+  c->t_last = t;
+}
+}  // namespace
+
 void StageTimer::begin(cudaStream_t s) {
   count = 0;
   launches = 0;
@@ -64,17 +92,40 @@ void StageTimer::begin(cudaStream_t s) {
 }
 
 void StageTimer::mark(const char* what, cudaStream_t s) {
+  if (device) {
+    if (dev_ctl) {
+      k_stage_mark<<<1, 1, 0, s>>>(dev_ctl, stage_index(what));
+      ++launches;
+    }
+    return;
+  }
   if (!on || count >= 256) return;
-  if (cudaEventCreate(&ev[count]) != cudaSuccess) return;
+  if (!ev_ready) {
+    for (int i = 0; i < 256; ++i)
+      if (cudaEventCreate(&ev[i]) != cudaSuccess) {
+        for (int j = 0; j < i; ++j) cudaEventDestroy(ev[j]);
+        return;
+      }
+    ev_ready = true;
+  }
   name[count] = what;
   cudaEventRecord(ev[count], s);
   ++count;
 }
 
+void StageTimer::release() {
+  if (ev_ready)
+    for (int i = 0; i < 256; ++i) cudaEventDestroy(ev[i]);
+  ev_ready = false;
+}
+
 void StageTimer::finish() {
   nstages = 0;
+  if (device) {
+    count = 0;
+    return;
+  }
   if (!on || count < 2) {
-    for (int i = 0; i < count; ++i) cudaEventDestroy(ev[i]);
     count = 0;
     return;
   }
@@ -96,7 +147,6 @@ void StageTimer::finish() {
   }
   if (std::getenv("MRRR_TIMING"))
     for (int k = 0; k < nstages; ++k) std::fprintf(stderr, "[mrrr timing] %-18s %10.3f ms\n", stage_name[k], stage_ms[k]);
-  for (int i = 0; i < count; ++i) cudaEventDestroy(ev[i]);
   count = 0;
 }
 
@@ -107,18 +157,23 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-  size_t ctl, prob, blk, node, pool_dl, pool_ul, ilist, lo, hi, gap, wval, znrm2, snode, sj, spos, state, bflag,
-      vscr;
+  size_t ctl, prob, blk, node, pool_dl, pool_ul, ilist, lwin, sched_cnt, sched_claim, lo, hi, gap, wval, znrm2,
+      snode, sj, spos, state, bflag, vscr;
   size_t total;
   int64_t max_blocks, max_nodes, max_slots, pool_rows, vscr_threads, vscr_rows;
 };
 
-// Threads of the eigenvector kernel (one vector at a time each): enough
-// resident warps to hide the division chains, but no more than there are
-// eigenpairs (each thread owns n_max doubles of scratch).
-int64_t vec_threads(const mrrr_plan* p, int64_t max_slots) {
+// Threads of the eigenvector kernel (persistent; one vector at a time per
+// thread): vec_blocks_per_sm CTAs of 128 per SM, no more than there are
+// eigenpairs, and -- each thread owning 2 n_max doubles of interleaved
+// scratch -- no more than fit in 16 GB of scratch, but never fewer than one
+// warp per SM sub-partition.
+int64_t vec_threads(const mrrr_plan* p, int64_t max_slots, int n_max) {
   const int64_t cap = (int64_t)p->nsm * std::max(1, p->opt.vec_blocks_per_sm) * 128;
-  return std::max<int64_t>(128, std::min(cap, (max_slots + 127) / 128 * 128));
+  const int64_t floor_t = (int64_t)p->nsm * 128;
+  const int64_t mem_t = ((int64_t)16 << 30) / (16 * (int64_t)std::max(n_max, 1)) / 128 * 128;
+  const int64_t t = std::min(cap, std::max(floor_t, mem_t));
+  return std::max<int64_t>(128, std::min(t, (max_slots + 127) / 128 * 128));
 }
 
 Layout make_layout(const mrrr_plan* p, int batch, int64_t n_total, int64_t k_total, int n_max) {
@@ -137,7 +192,7 @@ Layout make_layout(const mrrr_plan* p, int batch, int64_t n_total, int64_t k_tot
     pool_child = std::min(want, cap);
   }
   L.pool_rows = n_total + pool_child;
-  L.vscr_threads = vec_threads(p, L.max_slots);
+  L.vscr_threads = vec_threads(p, L.max_slots, n_max);
   L.vscr_rows = std::max(n_max, 1);
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -152,6 +207,9 @@ Layout make_layout(const mrrr_plan* p, int batch, int64_t n_total, int64_t k_tot
   L.pool_dl = take(sizeof(double2) * (size_t)L.pool_rows);
   L.pool_ul = take(sizeof(double2) * (size_t)L.pool_rows);
   L.ilist = take(sizeof(int64_t) * (size_t)L.max_slots);
+  L.lwin = take(sizeof(int64_t) * 2 * (size_t)((L.max_slots + 31) / 32));
+  L.sched_cnt = take(sizeof(int) * (size_t)kSchedSlots);
+  L.sched_claim = take(sizeof(int) * (size_t)L.max_slots);
 
   L.lo = take(sizeof(double) * (size_t)L.max_slots);
   L.hi = take(sizeof(double) * (size_t)L.max_slots);
@@ -163,9 +221,11 @@ Layout make_layout(const mrrr_plan* p, int batch, int64_t n_total, int64_t k_tot
   L.spos = take(sizeof(int) * (size_t)L.max_slots);
   L.state = take(sizeof(int) * (size_t)L.max_slots);
   L.bflag = take((size_t)L.max_slots);
-  // the vector scratch also holds the FP32 copy of the root rows (one
-  // float2 per row) during root bisection
-  L.vscr = take(sizeof(double) * std::max<size_t>((size_t)L.vscr_threads * (size_t)L.vscr_rows, (size_t)n_total));
+  // the vector scratch: two interleaved arrays (L+, and s then U-) of
+  // vscr_rows rows per thread; it also holds the FP32 copy of the root rows
+  // (one float2 per row) during root bisection
+  L.vscr = take(sizeof(double) *
+                std::max<size_t>(2 * (size_t)L.vscr_threads * (size_t)L.vscr_rows, (size_t)n_total));
   L.total = off;
   return L;
 }
@@ -181,6 +241,11 @@ Dev make_dev(const mrrr_plan* p, const Layout& L, void* ws, int batch, const dou
   v.rep_dl = reinterpret_cast<double2*>(b + L.pool_dl);
   v.rep_ul = reinterpret_cast<double2*>(b + L.pool_ul);
   v.ilist = reinterpret_cast<int64_t*>(b + L.ilist);
+  v.lwin = reinterpret_cast<int64_t*>(b + L.lwin);
+  v.sched_cnt = reinterpret_cast<int*>(b + L.sched_cnt);
+  v.sched_claim = reinterpret_cast<int*>(b + L.sched_claim);
+  v.max_chunks = L.max_slots;
+  v.nsm = p->nsm;
 
   v.max_list = L.max_slots;
   v.pool_cap = L.pool_rows;
@@ -215,16 +280,18 @@ Dev make_dev(const mrrr_plan* p, const Layout& L, void* ws, int batch, const dou
   v.max_bisect = o.max_bisect_steps;
   v.engine_ctas = o.engine_blocks_per_sm;
   v.width_scale = o.width_scale;
+  v.fixed_width = o.multisection_width;
+  v.root_side = o.root_side;
   return v;
 }
 
-Grid make_grid(const mrrr_plan* p, int64_t max_slots) {
+Grid make_grid(const mrrr_plan* p, int64_t max_slots, int n_max) {
   Grid g;
   g.nsm = p->nsm;
   g.tpb = std::max(32, std::min(1024, p->opt.threads_per_block));
   int64_t want = (max_slots + g.tpb - 1) / g.tpb;
   g.slot_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)p->nsm * 32));
-  g.vec_blocks = (int)(vec_threads(p, max_slots) / 128);
+  g.vec_blocks = (int)(vec_threads(p, max_slots, n_max) / 128);
   return g;
 }
 
@@ -232,48 +299,49 @@ mrrr_status cuda_status(cudaError_t e) { return e == cudaSuccess ? MRRR_OK : MRR
 
 // One solve enqueued on s.  device_levels: every level up to max_depth is
 // enqueued without host synchronisation and the level kernels return at
-// once after the tree is complete (used for graph capture); otherwise the
-// host reads the new-cluster count after each level and stops there.
+// once after the tree is complete; otherwise the host reads the new-cluster
+// count after each level and stops there.
 mrrr_status solve(mrrr_plan* p, const ProblemArgs& a, const double* d, const double* e, double* W, double* Z,
                   int64_t n_total, int64_t k_total, int n_max, void* ws, size_t ws_bytes, cudaStream_t s,
                   bool device_levels = false) {
   Layout L = make_layout(p, a.batch, n_total, k_total, n_max);
   if (!ws || ws_bytes < L.total) return MRRR_ERR_WORKSPACE;
   Dev v = make_dev(p, L, ws, a.batch, d, e, W, Z);
-  Grid g = make_grid(p, L.max_slots);
+  Grid g = make_grid(p, L.max_slots, n_max);
   p->last_ws = ws;
-  if (cudaMemsetAsync(v.ctl, 0, sizeof(Ctl), s) != cudaSuccess) return MRRR_ERR_CUDA;
+  p->last_graph = false;
+  if (cudaMemsetAsync(v.ctl, 0, sizeof(Ctl), s) != cudaSuccess ||
+      cudaMemsetAsync(v.sched_claim, 0, sizeof(int) * (size_t)v.max_chunks, s) != cudaSuccess)
+    return MRRR_ERR_CUDA;
   // Clusters from an earlier solve on this workspace must not leak into this
   // one: the per-slot arrays are fully rewritten by the setup kernels.
   StageTimer* tm = &p->timer;
   const bool timing_was = tm->on;
   if (std::getenv("MRRR_TIMING") && !device_levels) tm->on = true;
   if (device_levels) tm->on = false;  // no event records inside a capture
+  tm->device = false;
   set_stage_timer(tm);
   tm->begin(s);
   launch_setup(v, a, n_total, g, s);
   if (device_levels) {
     for (int level = 0; level <= p->opt.max_depth; ++level) {
-      launch_level_classify(v, level, g, s);
-      launch_level_children(v, level, g, s);
+      launch_level_classify(v, g, s);
+      launch_level_children(v, g, s);
     }
   }
-  int levels = 0;
   for (int level = 0; !device_levels && level <= p->opt.max_depth; ++level) {
-    launch_level_classify(v, level, g, s);
-    tm->mark("classify", s);
+    launch_level_classify(v, g, s);
     if (cudaMemcpyAsync(p->host_ctl, v.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {
       tm->on = false;
-      tm->finish();  // only releases the events recorded so far
+      tm->finish();
       tm->on = timing_was;
       set_stage_timer(nullptr);
       return MRRR_ERR_CUDA;
     }
-    ++levels;
     if (p->host_ctl->status != 0 && p->host_ctl->status != MRRR_ERR_NOCONV) break;
     if (p->host_ctl->level_new == 0) break;
-    launch_level_children(v, level, g, s);
+    launch_level_children(v, g, s);
   }
   launch_engine(v, 3, g, s);
   tm->mark("final_bisect", s);
@@ -282,12 +350,103 @@ mrrr_status solve(mrrr_plan* p, const ProblemArgs& a, const double* d, const dou
   tm->finish();
   set_stage_timer(nullptr);
   tm->on = timing_was;
-  (void)levels;
   return cuda_status(cudaGetLastError());
 }
 
+// The solve as one CUDA graph whose cluster levels run in a conditional
+// while node: setup, then the level body (classification, child
+// representations, refinement) repeated on the device for as long as the
+// last level made new clusters (k_level_end sets the condition), then the
+// final bisection and the vectors.  No host synchronisation and no level is
+// launched beyond the tree's depth.  Stage times come from device-clock
+// marks.  Returns MRRR_ERR_NOTIMPL when the runtime refuses a conditional
+// node (the caller then captures the unrolled form).
+mrrr_status capture_conditional(mrrr_plan* p, const ProblemArgs& a, const double* d, const double* e, double* W,
+                                double* Z, int64_t n_total, int64_t k_total, int n_max, void* ws,
+                                cudaGraph_t* out) {
+  *out = nullptr;
+  Layout L = make_layout(p, a.batch, n_total, k_total, n_max);
+  Dev v = make_dev(p, L, ws, a.batch, d, e, W, Z);
+  Grid g = make_grid(p, L.max_slots, n_max);
+  cudaStream_t cs = p->cap_stream;
+  const cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
+  cudaGraph_t graph = nullptr, tmp = nullptr;
+  if (cudaGraphCreate(&graph, 0) != cudaSuccess) return MRRR_ERR_CUDA;
+  StageTimer* tm = &p->timer;
+  const bool timing_was = tm->on;
+  tm->on = false;
+  tm->device = true;
+  tm->dev_ctl = v.ctl;
+  set_stage_timer(tm);
+  auto fail = [&](mrrr_status st) {
+    cudaStreamCaptureStatus cst;
+    if (cudaStreamIsCapturing(cs, &cst) == cudaSuccess && cst != cudaStreamCaptureStatusNone) {
+      cudaStreamEndCapture(cs, &tmp);
+    }
+    cudaGetLastError();
+    cudaGraphDestroy(graph);
+    tm->device = false;
+    tm->on = timing_was;
+    set_stage_timer(nullptr);
+    return st;
+  };
+  // part 1: control block, setup, root bisection
+  if (cudaStreamBeginCaptureToGraph(cs, graph, nullptr, nullptr, 0, mode) != cudaSuccess) return fail(MRRR_ERR_NOTIMPL);
+  cudaMemsetAsync(v.ctl, 0, sizeof(Ctl), cs);
+  cudaMemsetAsync(v.sched_claim, 0, sizeof(int) * (size_t)v.max_chunks, cs);
+  tm->begin(cs);
+  launch_setup(v, a, n_total, g, cs);
+  cudaStreamCaptureStatus cst;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  if (cudaStreamGetCaptureInfo(cs, &cst, nullptr, nullptr, &deps, nullptr, &ndeps) != cudaSuccess)
+    return fail(MRRR_ERR_CUDA);
+  cudaGraphNode_t dep_copy[16];
+  if (ndeps > 16) return fail(MRRR_ERR_NOTIMPL);
+  for (size_t i = 0; i < ndeps; ++i) dep_copy[i] = deps[i];
+  if (cudaStreamEndCapture(cs, &tmp) != cudaSuccess) return fail(MRRR_ERR_CUDA);
+  p->graph_part_launches[0] = tm->launches;
+  // part 2: the level loop
+  cudaGraphConditionalHandle cond;
+  if (cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault) != cudaSuccess)
+    return fail(MRRR_ERR_NOTIMPL);
+  cudaGraphNodeParams cp{};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = cond;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t loop;
+  if (cudaGraphAddNode(&loop, graph, dep_copy, nullptr, ndeps, &cp) != cudaSuccess) return fail(MRRR_ERR_NOTIMPL);
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  if (cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, mode) != cudaSuccess) return fail(MRRR_ERR_NOTIMPL);
+  launch_level_classify(v, g, cs, cond, 1);
+  launch_level_children(v, g, cs);
+  if (cudaStreamEndCapture(cs, &tmp) != cudaSuccess) return fail(MRRR_ERR_NOTIMPL);
+  p->graph_part_launches[1] = tm->launches - p->graph_part_launches[0];
+  // part 3: singletons to full accuracy, vectors
+  if (cudaStreamBeginCaptureToGraph(cs, graph, &loop, nullptr, 1, mode) != cudaSuccess) return fail(MRRR_ERR_NOTIMPL);
+  launch_engine(v, 3, g, cs);
+  tm->mark("final_bisect", cs);
+  launch_vectors(v, g, cs);
+  tm->mark("vectors", cs);
+  if (cudaStreamEndCapture(cs, &tmp) != cudaSuccess) return fail(MRRR_ERR_CUDA);
+  p->graph_part_launches[2] = tm->launches - p->graph_part_launches[0] - p->graph_part_launches[1];
+  tm->device = false;
+  tm->on = timing_was;
+  set_stage_timer(nullptr);
+  if (cudaGetLastError() != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    return MRRR_ERR_CUDA;
+  }
+  *out = graph;
+  return MRRR_OK;
+}
+
 // use_graph: capture the device-driven solve once per call signature on the
-// plan's own stream, then replay the graph on the caller's stream.
+// plan's own stream, then replay the graph on the caller's stream.  The
+// conditional-node form is tried first; where the runtime refuses it, every
+// level up to max_depth is captured (levels past the tree's depth return at
+// entry).
 mrrr_status solve_graph(mrrr_plan* p, const ProblemArgs& a, const double* d, const double* e, double* W, double* Z,
                         int64_t n_total, int64_t k_total, int n_max, void* ws, size_t ws_bytes, cudaStream_t s) {
   if (!ws || ws_bytes < make_layout(p, a.batch, n_total, k_total, n_max).total) return MRRR_ERR_WORKSPACE;
@@ -310,13 +469,20 @@ mrrr_status solve_graph(mrrr_plan* p, const ProblemArgs& a, const double* d, con
     }
     if (!p->cap_stream && cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
       return MRRR_ERR_CUDA;
-    if (cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return MRRR_ERR_CUDA;
-    const mrrr_status st = solve(p, a, d, e, W, Z, n_total, k_total, n_max, ws, ws_bytes, p->cap_stream, true);
     cudaGraph_t graph = nullptr;
-    const cudaError_t ce = cudaStreamEndCapture(p->cap_stream, &graph);
-    if (st != MRRR_OK || ce != cudaSuccess || !graph) {
+    p->timer.launches = 0;
+    mrrr_status st = capture_conditional(p, a, d, e, W, Z, n_total, k_total, n_max, ws, &graph);
+    p->graph_conditional = st == MRRR_OK;
+    if (st == MRRR_ERR_NOTIMPL) {
+      p->timer.launches = 0;
+      if (cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return MRRR_ERR_CUDA;
+      st = solve(p, a, d, e, W, Z, n_total, k_total, n_max, ws, ws_bytes, p->cap_stream, true);
+      const cudaError_t ce = cudaStreamEndCapture(p->cap_stream, &graph);
+      if (st == MRRR_OK && (ce != cudaSuccess || !graph)) st = MRRR_ERR_CUDA;
+    }
+    if (st != MRRR_OK) {
       if (graph) cudaGraphDestroy(graph);
-      return st != MRRR_OK ? st : MRRR_ERR_CUDA;
+      return st;
     }
     const cudaError_t ie = cudaGraphInstantiate(&p->exec, graph, 0);
     cudaGraphDestroy(graph);
@@ -326,6 +492,7 @@ mrrr_status solve_graph(mrrr_plan* p, const ProblemArgs& a, const double* d, con
     p->graph_launches = p->timer.launches;
   }
   p->last_ws = ws;
+  p->last_graph = true;
   p->timer.launches = p->graph_launches;
   p->timer.nstages = 0;
   return cuda_status(cudaGraphLaunch(p->exec, s));
@@ -352,7 +519,7 @@ mrrr_status mrrr_options_default(mrrr_options* opt) {
   opt->max_depth = 64;
   opt->max_bisect_steps = 256;
   opt->threads_per_block = 128;
-  opt->vec_blocks_per_sm = 8;
+  opt->vec_blocks_per_sm = 4;
   opt->cluster_rtol = 0x1p-40;
   opt->root_perturb = 64.0;
   opt->engine_blocks_per_sm = 2;
@@ -380,7 +547,11 @@ mrrr_status mrrr_plan_create(mrrr_plan** plan, const mrrr_options* opt) {
     if (opt->use_graph > 0) o.use_graph = 1;
     if (opt->engine_blocks_per_sm > 0) o.engine_blocks_per_sm = std::min(opt->engine_blocks_per_sm, 2);
     if (opt->width_scale > 0) o.width_scale = opt->width_scale;
+    if (opt->multisection_width > 0) o.multisection_width = opt->multisection_width;
+    if (opt->root_side > 0) o.root_side = opt->root_side;
   }
+  const int mw = o.multisection_width;
+  if (mw < 0 || mw > 32 || (mw & (mw - 1)) != 0 || o.root_side < 0 || o.root_side > 2) return MRRR_ERR_ARG;
   if (o.gap_tol >= 1.0 || o.classify_rtol >= 0.25 || o.threads_per_block % 32 != 0) return MRRR_ERR_ARG;
   int dev = 0, nsm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return MRRR_ERR_CUDA;
@@ -395,6 +566,8 @@ mrrr_status mrrr_plan_create(mrrr_plan** plan, const mrrr_options* opt) {
   p->cap_stream = nullptr;
   p->exec = nullptr;
   p->have_graph = false;
+  p->graph_conditional = false;
+  p->last_graph = false;
   p->graph_launches = 0;
   if (cudaMallocHost(&p->host_ctl, sizeof(Ctl)) != cudaSuccess) {
     delete p;
@@ -409,6 +582,7 @@ mrrr_status mrrr_plan_destroy(mrrr_plan* plan) {
   if (!plan) return MRRR_ERR_ARG;
   if (plan->have_graph) cudaGraphExecDestroy(plan->exec);
   if (plan->cap_stream) cudaStreamDestroy(plan->cap_stream);
+  plan->timer.release();
   cudaFreeHost(plan->host_ctl);
   delete plan;
   return MRRR_OK;
@@ -545,6 +719,11 @@ mrrr_status mrrr_get_status(mrrr_plan* plan, mrrr_stream stream, mrrr_info* out)
     out->twisted_solves = (int64_t)c.twisted_solves;
     out->levels = c.levels;
     for (int i = 0; i < 12; ++i) out->diag[i] = (int64_t)c.diag[i];
+    for (int i = 0; i < 4; ++i) {
+      out->sturm_counts[i] = (int64_t)c.eng_counts[i];
+      out->sturm_rows[i] = (int64_t)c.eng_rows[i];
+      out->warp_passes[i] = (int64_t)c.eng_passes[i];
+    }
   }
   return static_cast<mrrr_status>(c.status);
 }
@@ -560,6 +739,22 @@ mrrr_status mrrr_get_profile(const mrrr_plan* plan, mrrr_profile* out) {
   std::memset(out, 0, sizeof(*out));
   const StageTimer& t = plan->timer;
   out->launches = t.launches;
+  if (plan->last_graph && plan->last_ws) {
+    // graph replay: per-stage GPU time from the device-clock marks (the
+    // caller has synchronised the stream the graph ran on)
+    Ctl c;
+    if (cudaMemcpy(&c, plan->last_ws, sizeof(Ctl), cudaMemcpyDeviceToHost) != cudaSuccess) return MRRR_ERR_CUDA;
+    for (int k = 0; k < ST_COUNT; ++k) {
+      std::strncpy(out->name[k], kStageNames[k], 23);
+      out->ms[k] = (double)c.stage_ns[k] * 1e-6;
+    }
+    out->nstages = ST_COUNT;
+    // kernels executed: the loop body ran once per level
+    if (plan->graph_conditional)
+      out->launches = plan->graph_part_launches[0] + (int64_t)c.levels * plan->graph_part_launches[1] +
+                      plan->graph_part_launches[2];
+    return MRRR_OK;
+  }
   out->nstages = t.nstages;
   for (int k = 0; k < t.nstages && k < 32; ++k) {
     std::strncpy(out->name[k], t.stage_name[k], 23);

@@ -10,9 +10,10 @@
 // with few intervals each gets T lanes that evaluate T interior points per
 // pass over the representation (log2(T+1) bits per pass instead of one,
 // which shortens the chain of dependent passes); with many intervals T = 1
-// and no work is duplicated.  A warp holds 32/T lane groups and takes 32/T
-// consecutive list entries at a time (atomic counter) once all its groups
-// are done.  Every lane streams its node's (D, LLD) rows from L1/L2 with a
+// and no work is duplicated.  A warp holds 32/T lane groups and takes a
+// chunk of 32/T consecutive list entries at a time, once all its groups are
+// done, from the scheduler that spreads chunks over the SM sub-partitions
+// (sched_next).  Every lane streams its node's (D, LLD) rows from L1/L2 with a
 // register prefetch; the lanes of a group read the same rows.  The Sturm
 // counts are the division-free recurrence of count_step().  Root intervals
 // are first narrowed in FP32 (k_root32) and confirmed in FP64.
@@ -67,15 +68,6 @@ __device__ __forceinline__ bool slot_in_mode(const Dev& v, int64_t w, int level_
   return true;
 }
 
-__global__ void k_list_reset(Dev v) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    v.ctl->nlist = 0;
-    v.ctl->list_next = 0;
-    v.ctl->nlist2 = 0;
-    v.ctl->list_next2 = 0;
-  }
-}
-
 template <int MODE>
 __device__ __forceinline__ double mode_rtol(const Dev& v) {
   return MODE == MODE_ROOT || MODE == MODE_REFINE ? v.rtol : MODE == MODE_FINAL ? 2.0 * kEps : v.rtol_cluster;
@@ -99,32 +91,110 @@ __device__ __forceinline__ bool slot_is_long(const Dev& v, int64_t w) {
   return hi - lo > ldexp(goal, (int)kLongBits);
 }
 
-// Compaction of the wanted slots into the list (warp-aggregated appends):
-// long intervals from the front (nlist), short ones from the back (nlist2).
+// The work list: the wanted slots in slot order, long intervals from the
+// front (nlist of them), short ones from the back (nlist2), built by a scan
+// so that the list -- and with it which intervals share a warp -- is the same
+// on every run.  Three launches: per 32-slot window the counts of its long
+// and short entries, one CTA scanning them into offsets, then the writes.
 template <int MODE>
-__global__ void k_list(Dev v) {
+__device__ __forceinline__ void window_flags(const Dev& v, int64_t w, int64_t nslots, int level_begin, bool& lng,
+                                             bool& want) {
+  want = w < nslots && slot_in_mode<MODE>(v, w, level_begin);
+  lng = want && slot_is_long<MODE>(v, w);
+}
+
+template <int MODE>
+__global__ void k_list_count(Dev v) {
   if ((MODE == MODE_PREREFINE || MODE == MODE_REFINE) && v.ctl->done) return;
   const int lane = threadIdx.x & 31;
   const int64_t nslots = v.ctl->nslots;
   const int level_begin = v.ctl->level_begin;
-  for (int64_t w0 = gtid() - lane; w0 < nslots; w0 += gstride()) {
-    const int64_t w = w0 + lane;
-    const bool want = w < nslots && slot_in_mode<MODE>(v, w, level_begin);
-    const bool lng = want && slot_is_long<MODE>(v, w);
+  const int64_t nwin = (nslots + 31) / 32;
+  for (int64_t win = gtid() >> 5; win < nwin; win += gstride() >> 5) {
+    bool lng, want;
+    window_flags<MODE>(v, win * 32 + lane, nslots, level_begin, lng, want);
     const unsigned ml = __ballot_sync(0xffffffffu, lng);
     const unsigned ms = __ballot_sync(0xffffffffu, want && !lng);
-    if (!(ml | ms)) continue;
-    unsigned long long bl = 0, bs = 0;
-    if (lane == 0 && ml) bl = atomicAdd((unsigned long long*)&v.ctl->nlist, (unsigned long long)__popc(ml));
-    if (lane == 0 && ms) bs = atomicAdd((unsigned long long*)&v.ctl->nlist2, (unsigned long long)__popc(ms));
-    bl = __shfl_sync(0xffffffffu, bl, 0);
-    bs = __shfl_sync(0xffffffffu, bs, 0);
-    const unsigned below = (1u << lane) - 1u;
+    if (lane == 0) {
+      v.lwin[2 * win] = __popc(ml);
+      v.lwin[2 * win + 1] = __popc(ms);
+    }
+  }
+}
+
+constexpr int kScanThreads = 1024;
+
+// Exclusive scan of the window counts (one CTA): each thread takes a
+// contiguous run of windows, the per-thread sums are scanned in shared
+// memory, then the offsets are written back in place.
+__global__ void __launch_bounds__(kScanThreads) k_list_scan(Dev v, int mode) {
+  if ((mode == MODE_PREREFINE || mode == MODE_REFINE) && v.ctl->done) {
+    // levels enqueued past the end of the tree: an empty list, so that the
+    // engine launch that follows does nothing
+    if (threadIdx.x == 0) {
+      v.ctl->nlist = 0;
+      v.ctl->nlist2 = 0;
+    }
+    return;
+  }
+  __shared__ long long s_l[kScanThreads], s_s[kScanThreads];
+  const int64_t nwin = (v.ctl->nslots + 31) / 32;
+  const int64_t per = (nwin + kScanThreads - 1) / kScanThreads;
+  const int64_t a = threadIdx.x * per, b = min(nwin, a + per);
+  long long tl = 0, ts = 0;
+  for (int64_t w = a; w < b; ++w) {
+    tl += v.lwin[2 * w];
+    ts += v.lwin[2 * w + 1];
+  }
+  s_l[threadIdx.x] = tl;
+  s_s[threadIdx.x] = ts;
+  __syncthreads();
+  for (int off = 1; off < kScanThreads; off <<= 1) {  // inclusive Hillis-Steele scan
+    long long xl = 0, xs = 0;
+    if (threadIdx.x >= off) {
+      xl = s_l[threadIdx.x - off];
+      xs = s_s[threadIdx.x - off];
+    }
+    __syncthreads();
+    s_l[threadIdx.x] += xl;
+    s_s[threadIdx.x] += xs;
+    __syncthreads();
+  }
+  long long ol = s_l[threadIdx.x] - tl, os = s_s[threadIdx.x] - ts;
+  for (int64_t w = a; w < b; ++w) {
+    const long long cl = v.lwin[2 * w], cs = v.lwin[2 * w + 1];
+    v.lwin[2 * w] = ol;
+    v.lwin[2 * w + 1] = os;
+    ol += cl;
+    os += cs;
+  }
+  if (threadIdx.x == kScanThreads - 1) {
+    v.ctl->nlist = s_l[kScanThreads - 1];
+    v.ctl->nlist2 = s_s[kScanThreads - 1];
+    v.ctl->list_next = 0;
+    v.ctl->list_next2 = 0;
+  }
+}
+
+template <int MODE>
+__global__ void k_list_write(Dev v) {
+  if ((MODE == MODE_PREREFINE || MODE == MODE_REFINE) && v.ctl->done) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t nslots = v.ctl->nslots;
+  const int level_begin = v.ctl->level_begin;
+  const int64_t nwin = (nslots + 31) / 32;
+  const unsigned below = (1u << lane) - 1u;
+  for (int64_t win = gtid() >> 5; win < nwin; win += gstride() >> 5) {
+    const int64_t w = win * 32 + lane;
+    bool lng, want;
+    window_flags<MODE>(v, w, nslots, level_begin, lng, want);
+    const unsigned ml = __ballot_sync(0xffffffffu, lng);
+    const unsigned ms = __ballot_sync(0xffffffffu, want && !lng);
     if (lng) {
-      const long long at = (long long)bl + __popc(ml & below);
+      const long long at = v.lwin[2 * win] + __popc(ml & below);
       if (at < v.max_list) v.ilist[at] = w;
     } else if (want) {
-      const long long at = (long long)bs + __popc(ms & below);
+      const long long at = v.lwin[2 * win + 1] + __popc(ms & below);
       if (at < v.max_list) v.ilist[v.max_list - 1 - at] = w;
     }
   }
@@ -256,41 +326,46 @@ __device__ __forceinline__ void iv_load(const Dev& v, int64_t w, Iv& q) {
   }
 }
 
-// Evaluation point of lane pt (of T) of an interval in this pass; false when
-// the lane has no point this pass.
-__device__ __forceinline__ bool iv_tau(const Iv& q, int T, int pt, double& tau) {
+// Evaluation point of lane pos of a run of P lanes that share one bracket
+// (one interval's T lanes, or the lanes of consecutive intervals of one node
+// whose brackets coincide); false when the lane has no point this pass.
+// Confirming a bracket needs its two ends: with P >= 2 both in one pass,
+// with a single lane one end per pass (lower, then upper).
+__device__ __forceinline__ bool iv_tau(const Iv& q, int P, int pos, double& tau) {
   if (q.phase == PH_VERIFY) {
-    if (T >= 2) {
-      tau = pt == 0 ? q.lo : q.hi;
-      return pt < 2;
+    if (P >= 2) {
+      tau = pos == 0 ? q.lo : q.hi;
+      return pos < 2;
     }
-    tau = (q.tries & 1) ? q.hi : q.lo;  // one end per pass: lo, then hi
+    tau = (q.tries & 1) ? q.hi : q.lo;
     return true;
   }
-  tau = q.lo + (q.hi - q.lo) * ((double)(pt + 1) / (double)(T + 1));
+  tau = q.lo + (q.hi - q.lo) * ((double)(pos + 1) / (double)(P + 1));
   return true;
 }
 
-// Update after a pass.  kfirst: index of the first point whose count is
-// >= j (T when none); c0, c1: the counts of points 0 and 1.  Returns true
+// Update after a pass over a run of P points.  kfirst: index of the first
+// point whose count is >= j (P when none); c_lo, c_hi: the counts at the
+// run's points 0 and 1 (with P = 1, c_lo is the single count).  Returns true
 // when the interval is finished.
 template <int MODE>
-__device__ __forceinline__ bool iv_update(const Dev& v, int T, double rtol, int maxsteps, int kfirst, int c0,
-                                          int c1, Iv& q) {
+__device__ __forceinline__ bool iv_update(const Dev& v, int P, double rtol, int maxsteps, int kfirst, int c_lo,
+                                          int c_hi, Iv& q) {
   if (q.phase == PH_VERIFY) {
     bool ok_lo, ok_hi, decided;
-    if (T >= 2) {
-      ok_lo = c0 <= q.j - 1;
-      ok_hi = c1 >= q.j;
+    if (P >= 2) {
+      ok_lo = c_lo <= q.j - 1;
+      ok_hi = c_hi >= q.j;
       decided = true;
+      q.tries &= ~1;
     } else if ((q.tries & 1) == 0) {  // lower end just counted
-      ok_lo = c0 <= q.j - 1;
+      ok_lo = c_lo <= q.j - 1;
       ok_hi = true;
       decided = !ok_lo;
       if (ok_lo) q.tries |= 1;  // next: upper end
     } else {
       ok_lo = true;
-      ok_hi = c0 >= q.j;
+      ok_hi = c_lo >= q.j;
       decided = true;
       q.tries &= ~1;
     }
@@ -318,8 +393,8 @@ __device__ __forceinline__ bool iv_update(const Dev& v, int T, double rtol, int 
     return false;
   }
   const int k = kfirst;
-  const double nlo = k > 0 ? q.lo + (q.hi - q.lo) * ((double)k / (double)(T + 1)) : q.lo;
-  const double nhi = k < T ? q.lo + (q.hi - q.lo) * ((double)(k + 1) / (double)(T + 1)) : q.hi;
+  const double nlo = k > 0 ? q.lo + (q.hi - q.lo) * ((double)k / (double)(P + 1)) : q.lo;
+  const double nhi = k < P ? q.lo + (q.hi - q.lo) * ((double)(k + 1) / (double)(P + 1)) : q.hi;
   const bool stuck = !(nlo < nhi) || (nlo == q.lo && nhi == q.hi);
   q.lo = nlo;
   q.hi = nhi;
@@ -363,8 +438,13 @@ __device__ __forceinline__ int lane_count(const double2* __restrict__ dl, int m,
 }
 
 // Multisection width for a list of nlist intervals: the largest power of
-// two T <= 32 with 2 T nlist <= lanes_total.
-__device__ __forceinline__ int width_for(long long nlist, long long lanes_total) {
+// two T <= 32 with T nlist <= lanes_total.  lanes_total is one warp per SM
+// sub-partition (times width_scale): each sub-partition's FP64 unit takes
+// about 64 cycles per warp instruction whatever the number of active lanes,
+// and one warp's dependent count already keeps it busy, so more points per
+// interval only pay while they fill sub-partitions that would otherwise idle.
+__device__ __forceinline__ int width_for(long long nlist, long long lanes_total, int fixed) {
+  if (fixed > 0) return fixed;
   int T = 1;
   while (T < 32 && 2LL * T * nlist <= lanes_total) T *= 2;
   return T;
@@ -373,64 +453,110 @@ __device__ __forceinline__ int width_for(long long nlist, long long lanes_total)
 // Phase 0 drains the long intervals (front of the list), phase 1 the short
 // ones (back of the list), each with the width that its own length allows;
 // a warp moves on to phase 1 as soon as the long list is exhausted for it.
+//
+// Pooled points: consecutive lane groups of a warp whose intervals lie on the
+// same representation with the same bracket (cluster members refined from a
+// common parent bracket) form a run, and the run's k T lanes evaluate k T
+// points spread over that bracket.  A count at any point brackets every
+// member at once, so k members sharing a bracket narrow it (k T + 1)-fold per
+// pass instead of (T + 1)-fold each; each member then keeps the pair of
+// neighbouring points that brackets its own index.  With a fixed width
+// (options) runs are single groups: each interval's passes depend on nothing
+// but itself.
 template <int MODE>
 __global__ void __launch_bounds__(kEngThreads, kEngCtasPerSm) k_engine(Dev v) {
+  if ((MODE == MODE_PREREFINE || MODE == MODE_REFINE) && v.ctl->done) return;
   const int lane = threadIdx.x & 31;
   const long long nlong = min(v.ctl->nlist, (long long)v.max_list);
   const long long nshort = min(v.ctl->nlist2, (long long)v.max_list - nlong);
-  const long long lanes_total = (long long)((double)gridDim.x * blockDim.x * v.width_scale);
+  const long long lanes_total = (long long)((double)v.nsm * 4 * 32 * v.width_scale);
+  // chunks: the long intervals first, then the short ones, each part with
+  // the width its own length allows; a chunk is one warp's 32 / T intervals
+  const int T_long = width_for(nlong, lanes_total, v.fixed_width);
+  const int T_short = width_for(nshort, lanes_total, v.fixed_width);
+  const long long g_long = 32 / T_long, g_short = 32 / T_short;
+  const long long nch_long = (nlong + g_long - 1) / g_long;
+  const long long nchunks = nch_long + (nshort + g_short - 1) / g_short;
+  const long long total_warps = (long long)gridDim.x * (blockDim.x / 32);
+  const long long rank = sched_rank(v);
   const double rtol = mode_rtol<MODE>(v);
   const int maxsteps = v.max_bisect;
-  for (int phase = 0; phase < 2; ++phase) {
-    const long long nlist = phase == 0 ? nlong : nshort;
-    if (nlist == 0) continue;
-    unsigned long long* next = phase == 0 ? (unsigned long long*)&v.ctl->list_next
-                                          : (unsigned long long*)&v.ctl->list_next2;
-    const int T = width_for(nlist, lanes_total);
-    const int pt = lane % T, leader = lane - pt;
-    const unsigned gbits = T == 32 ? 0xffffffffu : (((1u << T) - 1u) << leader);
+  const bool pool = v.fixed_width == 0 && MODE != MODE_ROOT && MODE != MODE_FINAL;
+  const unsigned at_or_below = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
+  unsigned long long n_counts = 0, n_rows = 0, n_passes = 0;
+  bool first = true;
+  for (;;) {
+    // the warp's next chunk (consecutive list entries: neighbouring slots, so
+    // the same node or problem: the lanes share row lengths and often rows)
+    const long long chunk = sched_next(v, nchunks, total_warps, rank, first);
+    if (chunk < 0) break;
+    const bool is_long = chunk < nch_long;
+    const int T = is_long ? T_long : T_short;
+    const int pt = lane % T;
     const int groups = 32 / T, grp = lane / T;
+    const long long item = (is_long ? chunk : chunk - nch_long) * groups + grp;
+    const long long nlist = is_long ? nlong : nshort;
     Iv q{};
-    bool have = false, exhausted = false;
-    for (;;) {
-      // when every group of the warp is done, the warp takes the next
-      // `groups` consecutive list entries (neighbouring slots: the same node
-      // or problem, so the lanes share row lengths and often rows); an
-      // interval already converged on entry is finished at once
-      while (!exhausted && !__any_sync(0xffffffffu, have)) {
-        long long base = 0;
-        if (lane == 0) base = (long long)atomicAdd(next, (unsigned long long)groups);
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (base >= nlist) {
-          exhausted = true;
-          break;
+    bool have = false;
+    if (item < nlist) {
+      iv_load<MODE>(v, v.ilist[is_long ? item : v.max_list - 1 - item], q);
+      if (q.phase == PH_BISECT && converged(q.lo, q.hi, rtol, q.atol)) {
+        if (pt == 0) {  // already converged on entry
+          v.lo[q.slot] = q.lo;
+          v.hi[q.slot] = q.hi;
         }
-        const long long item = base + grp;
-        if (item < nlist) {
-          iv_load<MODE>(v, v.ilist[phase == 0 ? item : v.max_list - 1 - item], q);
-          if (q.phase == PH_BISECT && converged(q.lo, q.hi, rtol, q.atol)) {
-            if (pt == 0) {
-              v.lo[q.slot] = q.lo;
-              v.hi[q.slot] = q.hi;
-            }
-          } else {
-            have = true;
-          }
-        }
+      } else {
+        have = true;
       }
-      if (!__any_sync(0xffffffffu, have)) break;
+    }
+    while (__any_sync(0xffffffffu, have)) {
+      // runs: a group joins the run of the group before it when both hold an
+      // interval on the same rows, in the same phase, with the same bracket
+      bool join = false;
+      {
+        const double plo = __shfl_up_sync(0xffffffffu, q.lo, T);
+        const double phi = __shfl_up_sync(0xffffffffu, q.hi, T);
+        const long long pdl = __shfl_up_sync(0xffffffffu, (long long)q.dl, T);
+        const int pph = __shfl_up_sync(0xffffffffu, q.phase, T);
+        const int phave = __shfl_up_sync(0xffffffffu, (int)have, T);
+        join = pool && grp > 0 && have && phave && pdl == (long long)q.dl && pph == q.phase && plo == q.lo &&
+               phi == q.hi;
+      }
+      const unsigned starts = __ballot_sync(0xffffffffu, pt == 0 && !join);
+      const int run_lead = 31 - __clz(starts & at_or_below);
+      const unsigned above = starts & ~at_or_below;
+      const int P = (above ? __ffs(above) - 1 : 32) - run_lead;
+      const int pos = lane - run_lead;
       double tau = 0.0;
       bool act = have;
-      if (act) act = iv_tau(q, T, pt, tau);
+      if (act) act = iv_tau(q, P, pos, tau);
       int m_all = act ? q.m : 0;
       for (int o = 16; o; o >>= 1) m_all = max(m_all, __shfl_xor_sync(0xffffffffu, m_all, o));
       const int neg = lane_count(q.dl, q.m, m_all, tau, q.pivexp, q.pivmin, act);
-      // the group's counts: first point with count >= j, and points 0 and 1
-      const unsigned ge = __ballot_sync(0xffffffffu, act && neg >= q.j) & gbits;
-      const int kfirst = ge ? (__ffs(ge) - 1 - leader) : T;
-      const int c0 = __shfl_sync(0xffffffffu, neg, leader);
-      const int c1 = __shfl_sync(0xffffffffu, neg, T >= 2 ? leader + 1 : leader);
-      if (have && iv_update<MODE>(v, T, rtol, maxsteps, kfirst, c0, c1, q)) {
+      {
+        const unsigned am = __ballot_sync(0xffffffffu, act);
+        n_counts += __popc(am);
+        n_rows += (unsigned long long)__popc(am) * (unsigned long long)m_all;
+        ++n_passes;
+      }
+      // each member's first point with count >= j, by bisection over the
+      // run's points (P <= 32, six steps); the bracket found is valid even
+      // if rounding made the counts non-monotone: count < j at point kfirst-1
+      // and count >= j at point kfirst
+      int klo = 0, khi = P;
+      for (int it = 0; it < 6; ++it) {
+        const int mid = (klo + khi) >> 1;
+        const int c = __shfl_sync(0xffffffffu, neg, run_lead + min(mid, P - 1));
+        if (klo < khi) {
+          if (c >= q.j)
+            khi = mid;
+          else
+            klo = mid + 1;
+        }
+      }
+      const int c_lo = __shfl_sync(0xffffffffu, neg, run_lead);
+      const int c_hi = __shfl_sync(0xffffffffu, neg, P >= 2 ? run_lead + 1 : run_lead);
+      if (have && iv_update<MODE>(v, P, rtol, maxsteps, klo, c_lo, c_hi, q)) {
         if (pt == 0) {
           v.lo[q.slot] = q.lo;
           v.hi[q.slot] = q.hi;
@@ -439,13 +565,69 @@ __global__ void __launch_bounds__(kEngThreads, kEngCtasPerSm) k_engine(Dev v) {
       }
     }
   }
+  if (lane == 0 && n_passes) {
+    atomicAdd(&v.ctl->eng_counts[MODE], n_counts);
+    atomicAdd(&v.ctl->eng_rows[MODE], n_rows);
+    atomicAdd(&v.ctl->eng_passes[MODE], n_passes);
+  }
+}
+
+// Before the cluster stages: members of a new node whose brackets overlap
+// take the union of their brackets, so that the engine can pool their points
+// (the union contains each member's eigenvalue; REFINE confirms it in the
+// child anyway).  PREREFINE works on the node's two ends only; REFINE on
+// every member.  One thread per node of the current level.
+template <int MODE>
+__global__ void k_share_brackets(Dev v) {
+  if (v.ctl->done) return;
+  const int begin = v.ctl->level_begin;
+  const int end = min(v.ctl->nodes, v.max_nodes);
+  for (int64_t id = begin + gtid(); id < end; id += gstride()) {
+    const Node nd = v.node[id];
+    if (nd.depth < 0 || (MODE == MODE_REFINE && nd.rep < 0)) continue;
+    if (MODE == MODE_PREREFINE) {
+      const int64_t f = nd.first, l = nd.last;
+      if (l > f && v.hi[f] >= v.lo[l]) {
+        const double a = fmin(v.lo[f], v.lo[l]), b = fmax(v.hi[f], v.hi[l]);
+        v.lo[f] = v.lo[l] = a;
+        v.hi[f] = v.hi[l] = b;
+      }
+      continue;
+    }
+    int64_t s0 = nd.first;
+    double a = v.lo[s0], b = v.hi[s0];
+    for (int64_t w = nd.first + 1; w <= nd.last + 1; ++w) {
+      const bool close = w > nd.last || v.lo[w] > b;
+      if (close) {
+        if (w - 1 > s0)
+          for (int64_t t = s0; t < w; ++t) {
+            v.lo[t] = a;
+            v.hi[t] = b;
+          }
+        if (w <= nd.last) {
+          s0 = w;
+          a = v.lo[w];
+          b = v.hi[w];
+        }
+      } else {
+        a = fmin(a, v.lo[w]);
+        b = fmax(b, v.hi[w]);
+      }
+    }
+  }
 }
 
 template <int MODE>
 void launch_engine_mode(const Dev& v, const Grid& g, cudaStream_t s, int64_t n_total) {
-  k_list_reset<<<1, 32, 0, s>>>(v);
+  if ((MODE == MODE_PREREFINE || MODE == MODE_REFINE) && v.fixed_width == 0) {
+    k_share_brackets<MODE><<<g.slot_blocks, 128, 0, s>>>(v);
+    count_launch();
+  }
+  k_list_count<MODE><<<g.slot_blocks, 128, 0, s>>>(v);
   count_launch();
-  k_list<MODE><<<g.slot_blocks, 128, 0, s>>>(v);
+  k_list_scan<<<1, kScanThreads, 0, s>>>(v, MODE);
+  count_launch();
+  k_list_write<MODE><<<g.slot_blocks, 128, 0, s>>>(v);
   count_launch();
   if (MODE == MODE_ROOT) {
     k_root32_copy<<<g.slot_blocks, 256, 0, s>>>(v, n_total);
@@ -453,11 +635,22 @@ void launch_engine_mode(const Dev& v, const Grid& g, cudaStream_t s, int64_t n_t
     k_root32<<<g.slot_blocks, 128, 0, s>>>(v);
     count_launch();
   }
+  k_sched_reset<<<1, kSchedSlots, 0, s>>>(v);
+  count_launch();
   k_engine<MODE><<<g.nsm * max(1, min(kEngCtasPerSm, v.engine_ctas)), kEngThreads, 0, s>>>(v);
   count_launch();
 }
 
 }  // namespace
+
+__global__ void k_sched_reset(Dev v) {
+  for (int i = threadIdx.x; i < kSchedSlots; i += blockDim.x) v.sched_cnt[i] = 0;
+  if (threadIdx.x == 0) {
+    v.ctl->sched_gen += 1;
+    v.ctl->sched_dyn = 0;
+    v.ctl->sched_cleanup = 0;
+  }
+}
 
 void launch_engine(const Dev& v, int mode, const Grid& g, cudaStream_t s, int64_t n_total) {
   if (mode == 0)

@@ -100,6 +100,16 @@ struct Ctl {
   long long list_next2;   // next short entry to hand out
   int done;               // the tree is complete: later levels' kernels exit at once
   int pad4_;
+  unsigned long long eng_counts[4];  // interval engine, per mode: Sturm counts evaluated (lanes)
+  unsigned long long eng_rows[4];    //   rows those counts ran over
+  unsigned long long eng_passes[4];  //   warp passes (each costs its FP64 instructions whatever
+                                     //   the number of active lanes)
+  int sched_gen;                     // chunk scheduler: launch generation (claim stamps)
+  int pad5_;
+  unsigned long long sched_dyn;      //   chunks handed out past the ranked ones
+  unsigned long long sched_cleanup;  //   sweep over ranked chunks nobody claimed
+  unsigned long long stage_ns[16];  // per-stage GPU time from device-clock marks (graph solves)
+  unsigned long long t_last;        // global timer at the last mark
 };
 
 // Indices of Ctl::diag (mirrored in mrrr_info.diag).
@@ -108,12 +118,12 @@ enum : int {
   DIAG_ROOT_BISECT = 1,    // root bisection hit its step cap (intervals)
   DIAG_REFINE_BRACKET = 2, // child bracket could not be confirmed (intervals)
   DIAG_REFINE_BISECT = 3,  // child bisection hit its step cap (intervals)
-  DIAG_SPARE4 = 4,
+  DIAG_CHILD_WAVE2 = 4,    // clusters whose first candidate shifts all failed (second wave)
   DIAG_CHILD_GROWTH = 5,   // no child shift met the growth bound (clusters)
   DIAG_DEPTH = 6,          // depth-limit fallback (eigenvalues)
   DIAG_CAPACITY = 7,       // node table / pool full fallback (eigenvalues)
   DIAG_ORTH_FIX = 8,       // runs of neighbouring vectors re-orthogonalised
-  DIAG_SPARE9 = 9,
+  DIAG_CHILD_RESTORE = 9,  // child transforms computed again with stores
   DIAG_SPARE10 = 10,
   DIAG_SPARE11 = 11,
 };
@@ -129,6 +139,11 @@ struct Dev {
   int64_t pool_cap;   // rows
   int64_t* ilist;     // work list of the interval engine (slot indices)
   int64_t max_list;
+  int64_t* lwin;      // per 32-slot window: offsets of its long and short entries in the list
+  int* sched_cnt;     // chunk scheduler: warps seen per SM sub-partition (kSchedSlots)
+  int* sched_claim;   //   per chunk: generation of the launch that claimed it
+  int64_t max_chunks;
+  int nsm;            // SMs of the device
 
   int max_blocks;
   int max_nodes;
@@ -164,6 +179,8 @@ struct Dev {
   int max_bisect;
   int engine_ctas;      // engine CTAs per SM (1 or 2)
   double width_scale;   // multiplies the resident lanes when choosing the multisection width
+  int fixed_width;      // 0: width from the list length, brackets pooled; else fixed width, no pooling
+  int root_side;        // 0 nearer the wanted range, 1 left, 2 right
 };
 
 __device__ __forceinline__ void set_status(Ctl* c, int code) {
@@ -264,7 +281,71 @@ __device__ __forceinline__ int bisect_interval(const double2* __restrict__ dl, i
   return it;
 }
 
+// ---------------------------------------------------------------------------
+// Chunk scheduler of the persistent kernels (interval engine, eigenvectors).
+// Each SM sub-partition's FP64 unit takes about 64 cycles per warp
+// instruction whatever the number of active lanes, so a launch whose list has
+// c chunks of one warp's work each should put them on c different
+// sub-partitions (then on each a second one, ...).  The hardware places CTAs
+// and warps as it likes (with two CTAs per SM, CTA b is not on SM b mod nsm),
+// so each warp reads where it runs (%smid, %warpid mod 4), counts itself on
+// that sub-partition (k-th warp there), and gets the rank
+//   k * (4 nsmid) + 4 smid + subpartition,
+// i.e. ranks 0 .. 4 nsmid - 1 are one warp on each sub-partition.  A warp
+// first takes the chunk of its rank, then chunks past the number of warps
+// from a counter, then sweeps the ranked chunks that no warp claimed (ranks
+// of SMs that ran fewer warps).  Every chunk carries the generation of the
+// launch that claimed it (atomic exchange), so each is done exactly once.
+constexpr int kSchedSlots = 1024;  // sub-partition counters (4 per SM id)
+
+__device__ __forceinline__ long long sched_rank(const Dev& v) {
+  const int lane = threadIdx.x & 31;
+  long long rank = 0;
+  if (lane == 0) {
+    unsigned smid, wid, nsmid;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+    asm volatile("mov.u32 %0, %%warpid;" : "=r"(wid));
+    asm volatile("mov.u32 %0, %%nsmid;" : "=r"(nsmid));
+    const unsigned slot = (smid * 4u + (wid & 3u)) % (unsigned)kSchedSlots;
+    const int k = atomicAdd(&v.sched_cnt[slot], 1);
+    rank = (long long)k * (4LL * (long long)nsmid) + (long long)slot;
+  }
+  return __shfl_sync(0xffffffffu, rank, 0);
+}
+
+__device__ __forceinline__ bool sched_claim(const Dev& v, long long c, int gen) {
+  return atomicExch(&v.sched_claim[c], gen) != gen;
+}
+
+// Next chunk for this warp (warp-uniform), or -1 when none is left.
+__device__ __forceinline__ long long sched_next(const Dev& v, long long nchunks, long long total_warps,
+                                                long long rank, bool& first) {
+  const int lane = threadIdx.x & 31;
+  long long c = -1;
+  if (lane == 0) {
+    const int gen = v.ctl->sched_gen;
+    if (first && rank < nchunks && sched_claim(v, rank, gen)) c = rank;
+    const long long ranked = min(nchunks, total_warps);
+    while (c < 0) {
+      const long long d = total_warps + (long long)atomicAdd(&v.ctl->sched_dyn, 1ull);
+      if (d < nchunks) {
+        if (sched_claim(v, d, gen)) c = d;
+        continue;
+      }
+      const long long r = (long long)atomicAdd(&v.ctl->sched_cleanup, 1ull);
+      if (r >= ranked) break;
+      if (sched_claim(v, r, gen)) c = r;
+    }
+  }
+  first = false;
+  return __shfl_sync(0xffffffffu, c, 0);
+}
+
 __device__ __forceinline__ int64_t gtid() { return (int64_t)blockIdx.x * blockDim.x + threadIdx.x; }
+
+// Before each scheduled launch (one CTA of kSchedSlots threads): counters to
+// zero, a new generation for the claims.
+__global__ void k_sched_reset(Dev v);
 __device__ __forceinline__ int64_t gstride() { return (int64_t)gridDim.x * blockDim.x; }
 
 }  // namespace mrrr

@@ -21,13 +21,28 @@ struct ProblemArgs {
   int64_t ldz;
 };
 
-// Per-stage timing and launch counting of a solve: CUDA events recorded
-// between stages (when enabled) and summed by stage name.
+// The solver's stages, in launch order (names of the per-stage profile).
+enum StageId : int {
+  ST_PREP = 0, ST_ROOT, ST_BISECT_ROOT, ST_RANK, ST_CLASSIFY, ST_PREREFINE, ST_CHILDREP, ST_REFINE, ST_FINAL,
+  ST_VECTORS, ST_COUNT
+};
+extern const char* const kStageNames[ST_COUNT];
+int stage_index(const char* name);  // -1 for names outside the table ("start")
+
+// Per-stage timing and launch counting of a solve, summed by stage name.
+// Direct launches: CUDA events recorded between stages, from a pool created
+// once per plan (no event is created inside a timed solve).  Inside a CUDA
+// graph, where a level body runs once per loop iteration: a one-thread kernel
+// per stage boundary adds the GPU global timer's advance to the stage's
+// counter in the workspace (Ctl::stage_ns), read back by the profile call.
 struct StageTimer {
   bool on = false;
+  bool device = false;       // device-clock marks (graph capture)
+  Ctl* dev_ctl = nullptr;    // their accumulators
   int count = 0;
   int64_t launches = 0;
   cudaEvent_t ev[256];
+  bool ev_ready = false;
   const char* name[256];
   // results of the last solve
   int nstages = 0;
@@ -36,6 +51,7 @@ struct StageTimer {
   void begin(cudaStream_t s);
   void mark(const char* what, cudaStream_t s);
   void finish();
+  void release();
 };
 // The timer of the solve running on this host thread (set by the solve).
 StageTimer* stage_timer();
@@ -63,8 +79,11 @@ void launch_setup(const Dev& v, const ProblemArgs& a, int64_t n_total, const Gri
 
 // one cluster level: classification and, when clusters appeared, child
 // representations and refinement (second half launched by launch_level_children)
-void launch_level_classify(const Dev& v, int level, const Grid& g, cudaStream_t s);
-void launch_level_children(const Dev& v, int level, const Grid& g, cudaStream_t s);
+// (cond, use_cond: the condition of a CUDA graph's while node that runs one
+// level per iteration)
+void launch_level_classify(const Dev& v, const Grid& g, cudaStream_t s, cudaGraphConditionalHandle cond = 0,
+                           int use_cond = 0);
+void launch_level_children(const Dev& v, const Grid& g, cudaStream_t s);
 
 // interval engine: mode 0 root bisection, 1 cluster pre-refinement in the
 // parent, 2 refinement in the child, 3 singletons to full accuracy (see

@@ -258,12 +258,49 @@ __global__ void k_blocks(Dev v) {
   }
 }
 
-// One thread per block: Gershgorin bounds, root shift sigma at the end of the
-// spectrum nearer the wanted indices, L0 D0 L0^T = T - sigma I (definite),
-// retried with sigma pushed outward until every pivot has the right sign.
+// L D L^T = T_b - sigma I of a block by the recurrence D_1 = d_1 - sigma,
+// l_i = e_i / D_i, D_{i+1} = d_{i+1} - sigma - l_i e_i (store = write the
+// rows).  Returns whether every pivot has the sign of a definite
+// factorization (positive for a shift left of the spectrum, negative right
+// of it) and is finite.
+__device__ bool root_factor(const Dev& v, const Problem& q, int64_t lr0, int m, double sigma, bool left,
+                            bool store, double2* dl, double2* ul) {
+  double Dcur = scaled_d(v, q, lr0) - sigma;
+  for (int i = 0; i < m - 1; ++i) {
+    if (!(left ? Dcur > kPivmin : Dcur < -kPivmin) || !isfinite(Dcur)) return false;
+    const double ei = scaled_e(v, q, lr0 + i);
+    const double l = ei / Dcur;
+    const double LD = l * Dcur;
+    const double LLD = l * LD;
+    if (store) rep_store(dl, ul, i, RepRow{Dcur, LLD, l, LD});
+    Dcur = (scaled_d(v, q, lr0 + i + 1) - sigma) - LLD;
+  }
+  if (!(left ? Dcur > kPivmin : Dcur < -kPivmin) || !isfinite(Dcur)) return false;
+  if (store) rep_store(dl, ul, m - 1, RepRow{Dcur, 0.0, 0.0, 0.0});
+  return true;
+}
+
+constexpr int kRootTries = 12;
+
+// Shift t of the root ladder: the Gershgorin end, pushed outward by
+// 4^t 4 eps spdiam (t = 1..10), then by 5% of spdiam.
+__device__ __forceinline__ double root_shift(int t, double gl, double gu, double spdiam, bool left) {
+  double delta = (t == 0) ? 0.0 : spdiam * kEps * 4.0 * (double)(1LL << (2 * t));
+  if (t == kRootTries - 1) delta = 0.05 * spdiam + kPivmin;
+  return left ? gl - delta : gu + delta;
+}
+
+// One warp per block: Gershgorin bounds (lanes over rows), the root shift
+// sigma at the end of the spectrum nearer the wanted indices, and
+// L0 D0 L0^T = T - sigma I, definite.  Lane 0 factors at the first shift of
+// the ladder with stores while lanes 1..11 test the others; if the first
+// fails, the first that holds is factored again with stores.  The seeded
+// perturbation, the norm of the rows and the bracket counts also run across
+// the lanes, so the block costs one or two sequential passes over its rows.
 __global__ void k_root(Dev v) {
   const int nblocks = v.ctl->nblocks;
-  for (int64_t b = gtid(); b < nblocks; b += gstride()) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t b = gtid() >> 5; b < nblocks; b += gstride() >> 5) {
     Block bk = v.blk[b];
     const Problem q = v.prob[bk.prob];
     const int m = bk.m;
@@ -282,18 +319,20 @@ __global__ void k_root(Dev v) {
     nd.gapr = INFINITY;
     nd.pivmin = kPivmin;
     if (m == 1) {
-      double d0 = scaled_d(v, q, lr0);
-      rep_store(dl, ul, 0, RepRow{0.0, 0.0, 0.0, 0.0});
-      nd.sigma_rel = nd.sigma_abs = d0;
-      nd.spdiam = 0.0;
-      bk.gl = bk.gu = 0.0;
-      v.blk[b] = bk;
-      v.node[b] = nd;
-      v.lo[bk.slot0] = v.hi[bk.slot0] = 0.0;
+      if (lane == 0) {
+        double d0 = scaled_d(v, q, lr0);
+        rep_store(dl, ul, 0, RepRow{0.0, 0.0, 0.0, 0.0});
+        nd.sigma_rel = nd.sigma_abs = d0;
+        nd.spdiam = 0.0;
+        bk.gl = bk.gu = 0.0;
+        v.blk[b] = bk;
+        v.node[b] = nd;
+        v.lo[bk.slot0] = v.hi[bk.slot0] = 0.0;
+      }
       continue;
     }
     double gl = INFINITY, gu = -INFINITY;
-    for (int i = 0; i < m; ++i) {
+    for (int i = lane; i < m; i += 32) {
       double r = 0.0;
       if (i > 0) r += fabs(scaled_e(v, q, lr0 + i - 1));
       if (i + 1 < m) r += fabs(scaled_e(v, q, lr0 + i));
@@ -301,74 +340,76 @@ __global__ void k_root(Dev v) {
       gl = fmin(gl, di - r);
       gu = fmax(gu, di + r);
     }
+    for (int o = 16; o; o >>= 1) {
+      gl = fmin(gl, __shfl_xor_sync(0xffffffffu, gl, o));
+      gu = fmax(gu, __shfl_xor_sync(0xffffffffu, gu, o));
+    }
     const double spdiam = gu - gl;
     const double gmax = fmax(fabs(gl), fabs(gu));
-    const bool left = (bk.js + bk.je) <= (m + 1);  // wanted range in the lower half
-    double sigma = left ? gl : gu;
-    bool ok = false;
-    for (int t = 0; t < 12 && !ok; ++t) {
-      double delta = (t == 0) ? 0.0 : spdiam * kEps * 4.0 * (double)(1LL << (2 * t));
-      if (t == 11) delta = 0.05 * spdiam + kPivmin;
-      sigma = left ? gl - delta : gu + delta;
-      double Dcur = scaled_d(v, q, lr0) - sigma;
-      ok = true;
-      for (int i = 0; i < m - 1; ++i) {
-        if (!(left ? Dcur > kPivmin : Dcur < -kPivmin) || !isfinite(Dcur)) {
-          ok = false;
-          break;
-        }
-        double ei = scaled_e(v, q, lr0 + i);
-        double l = ei / Dcur;
-        double LD = l * Dcur;
-        double LLD = l * LD;
-        rep_store(dl, ul, i, RepRow{Dcur, LLD, l, LD});
-        Dcur = (scaled_d(v, q, lr0 + i + 1) - sigma) - LLD;
-      }
-      if (ok && (!(left ? Dcur > kPivmin : Dcur < -kPivmin) || !isfinite(Dcur))) ok = false;
-      if (ok) rep_store(dl, ul, m - 1, RepRow{Dcur, 0.0, 0.0, 0.0});
-    }
-    if (!ok) {
+    // wanted range in the lower half, unless the side is fixed by the options
+    const bool left = v.root_side == 1 ? true : v.root_side == 2 ? false : (bk.js + bk.je) <= (m + 1);
+    bool ok_t = false;
+    if (lane < kRootTries) ok_t = root_factor(v, q, lr0, m, root_shift(lane, gl, gu, spdiam, left), left, lane == 0,
+                                              dl, ul);
+    const unsigned okm = __ballot_sync(0xffffffffu, ok_t);
+    const int t = okm ? __ffs(okm) - 1 : kRootTries - 1;
+    const double sigma = root_shift(t, gl, gu, spdiam, left);
+    if (t > 0 && lane == 0) root_factor(v, q, lr0, m, sigma, left, true, dl, ul);
+    if (!okm && lane == 0) {
       set_status(v.ctl, MRRR_ERR_NOCONV);
       diag(v.ctl, DIAG_ROOT_SHIFT);
     }
+    __syncwarp();
     // Seeded random relative perturbation of the root representation by a
     // few ulps (D_i and l_i times 1 + pert*eps*u, u in [-1,1) from a
-    // counter-based generator on the global row), which breaks the exact
-    // coincidence of eigenvalues of identical glued blocks (Dhillon, Parlett
-    // and Voemel, "Glued matrices and the MRRR algorithm", 2005).
-    if (v.root_perturb > 0.0) {
-      // at most m/8 ulps: the eigenvalue budget 4 m eps ||T|| is tight for
-      // small blocks, and glued copies only matter for large ones
-      const double amp = fmin(v.root_perturb, m / 8.0) * kEps;
-      for (int i = 0; i < m; ++i) {
-        const uint64_t row = (uint64_t)(bk.row0 + i);
-        double u1 = uniform_pm1(splitmix64(2 * row));
-        double u2 = uniform_pm1(splitmix64(2 * row + 1));
-        RepRow r = rep_row(dl, ul, i);
+    // counter-based generator on the row within the problem, so that a
+    // problem gets the same representation alone or in a batch), which breaks
+    // the exact coincidence of eigenvalues of identical glued blocks
+    // (Dhillon, Parlett and Voemel, "Glued matrices and the MRRR algorithm",
+    // 2005).  Rows are independent: lanes over rows.
+    double R = 0.0;
+    const double amp = v.root_perturb > 0.0 ? fmin(v.root_perturb, m / 8.0) * kEps : 0.0;
+    // at most m/8 ulps: the eigenvalue budget 4 m eps ||T|| is tight for
+    // small blocks, and glued copies only matter for large ones
+    for (int i = lane; i < m; i += 32) {
+      RepRow r = rep_row(dl, ul, i);
+      if (amp > 0.0) {
+        const uint64_t row = (uint64_t)(lr0 + i);
+        const double u1 = uniform_pm1(splitmix64(2 * row));
+        const double u2 = uniform_pm1(splitmix64(2 * row + 1));
         r.D *= 1.0 + amp * u1;
         r.l *= 1.0 + amp * u2;
         r.LD = r.l * r.D;
         r.LLD = r.l * r.LD;
         rep_store(dl, ul, i, r);
       }
+      R = fmax(R, fmax(fabs(r.D), fabs(r.LLD)));
     }
-    double R = 0.0;
-    for (int i = 0; i < m; ++i) {
-      const double2 x = dl[i];
-      R = fmax(R, fmax(fabs(x.x), fabs(x.y)));
-    }
+    for (int o = 16; o; o >>= 1) R = fmax(R, __shfl_xor_sync(0xffffffffu, R, o));
+    __syncwarp();
     nd.pivmin = pivmin_for(R);
-    // initial bracket in root coordinates, checked with Sturm counts
-    double pad = 4.0 * kEps * m * (gmax + spdiam) + 4.0 * kPivmin;
-    double lo = gl - sigma - pad, hi = gu - sigma + pad;
-    for (int t = 0; t < 60 && negcount(dl, m, lo, nd.pivmin) > 0; ++t) lo -= (hi - lo);
-    for (int t = 0; t < 60 && negcount(dl, m, hi, nd.pivmin) < m; ++t) hi += (hi - lo);
-    bk.gl = lo;
-    bk.gu = hi;
-    nd.sigma_rel = nd.sigma_abs = sigma;
-    nd.spdiam = spdiam;
-    v.blk[b] = bk;
-    v.node[b] = nd;
+    // initial bracket in root coordinates, checked with Sturm counts: lane 0
+    // moves the lower end down, lane 1 the upper end up
+    const double pad = 4.0 * kEps * m * (gmax + spdiam) + 4.0 * kPivmin;
+    const double lo0 = gl - sigma - pad, hi0 = gu - sigma + pad;
+    double x = lane == 0 ? lo0 : hi0;
+    if (lane < 2) {
+      const double step = hi0 - lo0;
+      for (int k = 0; k < 60; ++k) {
+        const int c = negcount(dl, m, x, nd.pivmin);
+        if (lane == 0 ? c == 0 : c == m) break;
+        x += (lane == 0 ? -step : step) * (double)(1LL << k);
+      }
+    }
+    const double lo = __shfl_sync(0xffffffffu, x, 0), hi = __shfl_sync(0xffffffffu, x, 1);
+    if (lane == 0) {
+      bk.gl = lo;
+      bk.gu = hi;
+      nd.sigma_rel = nd.sigma_abs = sigma;
+      nd.spdiam = spdiam;
+      v.blk[b] = bk;
+      v.node[b] = nd;
+    }
   }
 }
 
@@ -412,7 +453,7 @@ void launch_setup(const Dev& v, const ProblemArgs& a, int64_t n_total, const Gri
   k_blocks<<<std::max(wb, 1), 128, 0, s>>>(v);
   count_launch();
   mark_stage("prep", s);
-  k_root<<<std::max(pb, 1), 128, 0, s>>>(v);
+  k_root<<<std::max(wb, 1), 128, 0, s>>>(v);
   count_launch();
   mark_stage("root", s);
   launch_engine(v, 0, g, s, n_total);

@@ -153,8 +153,7 @@ __global__ void __launch_bounds__(kRootThreads) k_static_root(int n, const doubl
 // representation in the scratch rows to full accuracy (width at most 2 eps
 // relative, or the two ends adjacent in floating point).  Device-side errors
 // give NaN eigenvalues.
-__global__ void k_static_bisect(int n, const double* __restrict__ d, int il, int iu, double* __restrict__ W,
-                                const double* scratch) {
+__global__ void k_static_bisect(int n, int il, int iu, double* __restrict__ W, const double* scratch) {
   const int k = iu - il + 1;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= k) return;
@@ -178,7 +177,8 @@ double* g_addr[kMaxDevices] = {};
 
 // Device address of the scratch array on the current device, looked up once
 // per device (the host-side symbol is only a stand-in and must never be
-// passed to a kernel).
+// passed to a kernel).  The cached address belongs to the device's primary
+// context: it does not survive cudaDeviceReset (see the header).
 mrrr_status scratch_address(double** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MRRR_ERR_CUDA;
@@ -206,7 +206,7 @@ extern "C" mrrr_status mrrr_eigenvalues_static(int n, const double* d, const dou
   k_static_root<<<1, kRootThreads, 0, s>>>(n, d, e, il, iu, scratch);
   if (cudaGetLastError() != cudaSuccess) return MRRR_ERR_CUDA;
   const int k = iu - il + 1;
-  k_static_bisect<<<(k + 127) / 128, 128, 0, s>>>(n, d, il, iu, W, scratch);
+  k_static_bisect<<<(k + 127) / 128, 128, 0, s>>>(n, il, iu, W, scratch);
   if (cudaGetLastError() != cudaSuccess) return MRRR_ERR_CUDA;
   return MRRR_OK;
 }

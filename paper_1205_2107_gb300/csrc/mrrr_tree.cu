@@ -23,12 +23,19 @@ __global__ void k_level_start(Dev v) {
 // After a level's classification: the tree is complete when the level made
 // no new cluster (or a fatal error was recorded); the kernels of all later
 // levels then return at entry, so the levels can be enqueued without the
-// host reading the count in between.
-__global__ void k_level_end(Dev v, int level) {
-  if (threadIdx.x == 0 && blockIdx.x == 0 && !v.ctl->done) {
-    v.ctl->levels = level + 1;
-    const int st = v.ctl->status;
-    if (v.ctl->level_new == 0 || (st != 0 && st != MRRR_ERR_NOCONV)) v.ctl->done = 1;
+// host reading the count in between.  The current level is ctl->levels (the
+// levels finished so far), so one captured level can be replayed by a graph
+// loop; inside a CUDA graph's conditional while node (use_cond) this kernel
+// also sets the loop's condition: one more level while the tree is not done.
+__global__ void k_level_end(Dev v, cudaGraphConditionalHandle cond, int use_cond) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    if (!v.ctl->done) {
+      const int level = v.ctl->levels;
+      v.ctl->levels = level + 1;
+      const int st = v.ctl->status;
+      if (v.ctl->level_new == 0 || (st != 0 && st != MRRR_ERR_NOCONV) || level + 1 > v.max_depth) v.ctl->done = 1;
+    }
+    if (use_cond) cudaGraphSetConditional(cond, v.ctl->done ? 0u : 1u);
   }
 }
 
@@ -42,8 +49,9 @@ __global__ void k_level_end(Dev v, int level) {
 // 1e-3 (fewer, shallower cluster levels): the floor gap_tol defaults to 1e-4.
 constexpr double kSmallBlockTol = 1.0;
 
-__global__ void k_classify_flags(Dev v, int level) {
+__global__ void k_classify_flags(Dev v) {
   if (v.ctl->done) return;
+  const int level = v.ctl->levels;
   const int64_t nslots = v.ctl->nslots;
   for (int64_t w = gtid(); w < nslots; w += gstride()) {
     if (v.state[w] != SLOT_ACTIVE) continue;
@@ -62,8 +70,9 @@ __global__ void k_classify_flags(Dev v, int level) {
 }
 
 // Runs between boundaries: length 1 = singleton, otherwise a new child node.
-__global__ void k_classify_runs(Dev v, int level) {
+__global__ void k_classify_runs(Dev v) {
   if (v.ctl->done) return;
+  const int level = v.ctl->levels;
   const int64_t nslots = v.ctl->nslots;
   for (int64_t w = gtid(); w < nslots; w += gstride()) {
     if (v.state[w] != SLOT_ACTIVE) continue;
@@ -161,6 +170,39 @@ __device__ double dstqds_child(const double2* __restrict__ pdl, const double2* _
   return kStore ? growth : gd;
 }
 
+// The transform of dstqds_child with the stores predicated on `store`: every
+// lane of a warp runs the same instructions whether it stores or not (two
+// template instances in one warp would run one after the other).  Returns
+// max(|D+_i|, |LLD+_i|); growth_d receives max|D+_i| (infinite when a pivot
+// is not finite).
+__device__ double dstqds_child_pred(const double2* __restrict__ pdl, const double2* __restrict__ pul,
+                                    double2* __restrict__ cdl, double2* __restrict__ cul, int m, double sigma,
+                                    double pivmin, bool store, double* growth_d) {
+  double s = -sigma;
+  double gd = 0.0, growth = 0.0;
+  for (int i = 0; i < m - 1; ++i) {
+    const RepRow r = rep_row(pdl, pul, i);
+    double dp = r.D + s;
+    if (fabs(dp) < pivmin) dp = -pivmin;
+    const double lp = r.LD / dp;
+    s = fma(lp, r.l * s, -sigma);
+    gd = fmax(gd, fabs(dp));
+    const double ldp = lp * dp;
+    const double lldp = lp * ldp;
+    if (store) rep_store(cdl, cul, i, RepRow{dp, lldp, lp, ldp});
+    growth = fmax(growth, fabs(lldp));
+  }
+  double dp = pdl[m - 1].x + s;
+  if (fabs(dp) < pivmin) dp = -pivmin;
+  if (store) rep_store(cdl, cul, m - 1, RepRow{dp, 0.0, 0.0, 0.0});
+  gd = fmax(gd, fabs(dp));
+  if (!isfinite(gd)) gd = INFINITY;
+  growth = fmax(growth, gd);
+  if (!isfinite(growth)) growth = INFINITY;
+  *growth_d = gd;
+  return growth;
+}
+
 constexpr int kShiftTries = 10;  // per side
 
 // Candidate shift t (0 .. 2 kShiftTries - 1) of a cluster: even t the left
@@ -183,51 +225,124 @@ __device__ __forceinline__ void set_child(Dev& v, int64_t id, Node c, const Node
   v.node[id] = c;
 }
 
-// Child representations, phase 1: one thread per new node reserves its rows
-// in the representation pool and builds the transform for the first
-// candidate shift (the left end of the cluster, smallest offset) with the
-// stores done in the same pass.  It is kept when its element growth max|D+|
-// is at most 8 spdiam; otherwise the node is marked for phase 2.  Nodes
-// whose rows do not fit take the fallback (their vectors at the parent).
+// Child representations, first wave.  The candidate shifts are tried in
+// ladder order 0, 1, 2, 3, 4, 8, 9, 18, 19 (child_shift); the first whose
+// element growth max|D+| is at most 8 spdiam is taken, else the one with the
+// smallest growth (counted in the diagnostics).  A group of L lanes per new
+// node (L from the number of nodes of the level: up to two warps per SM
+// sub-partition, so that the extra lanes cost no time) evaluates the first
+// min(L, 9) candidates in one pass over the parent's rows.  Each transform
+// is a sequential recurrence, so a level with few clusters is bound by the
+// latency of one pass: trying every candidate at once replaces up to three
+// passes (first candidate, the others, the winner again with stores) by one.
+// Candidate 0 is always computed with stores; when the pool has room, every
+// candidate of the group stores into rows of its own and the winner's rows
+// become the child (the others stay unused in the pool); otherwise a winner
+// other than candidate 0 is computed once more with stores.  A node whose
+// evaluated candidates all fail before the whole ladder was tried goes to
+// the second wave (k_childrep).  Nodes whose rows do not fit take the
+// fallback (their vectors at the parent).  The choice is the same whatever
+// L is, so the child representation is too.
+constexpr int kLadder = 9;
+__constant__ int kLadderCands[kLadder] = {0, 1, 2, 3, 4, 8, 9, 18, 19};
+
+__device__ __forceinline__ void child_fallback(Dev& v, int64_t id, Node c) {
+  set_status(v.ctl, MRRR_ERR_QUEUE);
+  // vectors of these slots are taken at the parent node
+  for (int64_t t = c.first; t <= c.last; ++t) {
+    v.state[t] = SLOT_FALLBACK;
+    v.snode[t] = c.parent;
+    double a = (t == c.first) ? c.gapl : v.lo[t] - v.hi[t - 1];
+    double b = (t == c.last) ? c.gapr : v.lo[t + 1] - v.hi[t];
+    v.gap[t] = fmax(fmin(a, b), 0.0);
+  }
+  atomicAdd(&v.ctl->fallbacks, (unsigned long long)(c.last - c.first + 1));
+  diag(v.ctl, DIAG_CAPACITY, (unsigned long long)(c.last - c.first + 1));
+  c.rep = -1;
+  c.depth = -1;  // inert
+  v.node[id] = c;
+}
+
 __global__ void k_childrep_first(Dev v) {
   if (v.ctl->done) return;
   const int begin = v.ctl->level_begin;
   const int end = min(v.ctl->nodes, v.max_nodes);
-  for (int64_t id = begin + gtid(); id < end; id += gstride()) {
-    Node c = v.node[id];
-    const Node p = v.node[c.parent];
-    const int m = v.blk[c.block].m;
-    const int64_t base =
-        (int64_t)atomicAdd((unsigned long long*)&v.ctl->pool_top, (unsigned long long)m);
-    atomicMax((unsigned long long*)&v.ctl->pool_need, (unsigned long long)(base + m));
-    if (base + m > v.pool_cap) {
-      set_status(v.ctl, MRRR_ERR_QUEUE);
-      // vectors of these slots are taken at the parent node
-      for (int64_t t = c.first; t <= c.last; ++t) {
-        v.state[t] = SLOT_FALLBACK;
-        v.snode[t] = c.parent;
-        double a = (t == c.first) ? c.gapl : v.lo[t] - v.hi[t - 1];
-        double b = (t == c.last) ? c.gapr : v.lo[t + 1] - v.hi[t];
-        v.gap[t] = fmax(fmin(a, b), 0.0);
+  const int N = end - begin;
+  if (N <= 0) return;
+  const long long lanes = (long long)v.nsm * 4 * 32 * 2;
+  int L = 1;
+  while (L < 16 && (long long)N * L * 2 <= lanes) L *= 2;
+  const int ncand = min(L, kLadder);
+  const int lane = threadIdx.x & 31;
+  const int gl = lane % L, leader = lane - gl, per_warp = 32 / L;
+  const unsigned gbits = L == 32 ? 0xffffffffu : (((1u << L) - 1u) << leader);
+  const int64_t warp = gtid() >> 5, nwarps = gstride() >> 5;
+  for (int64_t id0 = begin + warp * per_warp; id0 < end; id0 += nwarps * per_warp) {
+    const int64_t id = id0 + lane / L;
+    const bool mine = id < end;
+    Node c{};
+    Node p{};
+    int m = 0;
+    int64_t base = -1;
+    bool multi = false;
+    if (mine) {
+      c = v.node[id];
+      p = v.node[c.parent];
+      m = v.blk[c.block].m;
+      if (gl == 0) {
+        // rows for every candidate when the pool keeps half its room free
+        multi = ncand > 1 && v.ctl->pool_top + (int64_t)N * ncand * m <= v.pool_cap / 2;
+        const int64_t rows = (int64_t)(multi ? ncand : 1) * m;
+        base = (int64_t)atomicAdd((unsigned long long*)&v.ctl->pool_top, (unsigned long long)rows);
+        atomicMax((unsigned long long*)&v.ctl->pool_need, (unsigned long long)(base + rows));
+        if (base + rows > v.pool_cap) base = -1;
       }
-      atomicAdd(&v.ctl->fallbacks, (unsigned long long)(c.last - c.first + 1));
-      diag(v.ctl, DIAG_CAPACITY, (unsigned long long)(c.last - c.first + 1));
-      c.rep = -1;
-      c.depth = -1;  // inert
+    }
+    base = __shfl_sync(0xffffffffu, base, leader);
+    multi = __shfl_sync(0xffffffffu, (int)multi, leader) != 0;
+    const bool live = mine && base >= 0;
+    if (mine && base < 0 && gl == 0) child_fallback(v, id, c);
+    const bool cand = live && gl < ncand;
+    const int t = cand ? kLadderCands[gl] : 0;
+    double sigma = 0.0, gd = INFINITY, R = 0.0;
+    const bool stored = cand && (multi || gl == 0);
+    if (cand) {
+      sigma = child_shift(t, v.lo[c.first], v.hi[c.last], p.pivmin);
+      const int64_t at = base + (multi ? (int64_t)gl * m : 0);
+      R = dstqds_child_pred(v.rep_dl + p.rep, v.rep_ul + p.rep, v.rep_dl + at, v.rep_ul + at, m, sigma, p.pivmin,
+                            stored, &gd);
+    }
+    const bool ok = cand && gd <= 8.0 * c.spdiam;
+    const unsigned okmask = __ballot_sync(0xffffffffu, ok) & gbits;
+    // smallest growth in the group, lowest candidate on ties
+    double bg = gd;
+    int bl = gl;
+    for (int o = L / 2; o; o >>= 1) {
+      const double og = __shfl_xor_sync(0xffffffffu, bg, o);
+      const int ol = __shfl_xor_sync(0xffffffffu, bl, o);
+      if (og < bg || (og == bg && ol < bl)) bg = og, bl = ol;
+    }
+    int win = okmask ? __ffs(okmask) - 1 - leader : (ncand == kLadder ? bl : -1);
+    const double gd0 = __shfl_sync(0xffffffffu, gd, leader);
+    const double sig_w = __shfl_sync(0xffffffffu, sigma, leader + max(win, 0));
+    const double R_w = __shfl_sync(0xffffffffu, R, leader + max(win, 0));
+    if (!live || gl != 0) continue;
+    if (win < 0) {  // second wave: the rest of the ladder
+      c.rep = base;
+      c.pad_ = 1;
+      c.sigma_rel = gd0;  // growth of the first candidate, for the second wave
       v.node[id] = c;
+      diag(v.ctl, DIAG_CHILD_WAVE2);
       continue;
     }
-    const double sigma = child_shift(0, v.lo[c.first], v.hi[c.last], p.pivmin);
-    double gd;
-    const double R = dstqds_child<true>(v.rep_dl + p.rep, v.rep_ul + p.rep, v.rep_dl + base, v.rep_ul + base, m,
-                                        sigma, p.pivmin, &gd);
-    if (gd <= 8.0 * c.spdiam) {
-      set_child(v, id, c, p, base, sigma, R);
+    if (!okmask) diag(v.ctl, DIAG_CHILD_GROWTH);
+    if (multi || win == 0) {
+      set_child(v, id, c, p, base + (multi ? (int64_t)win * m : 0), sig_w, R_w);
     } else {
-      c.rep = base;
-      c.pad_ = 1;           // phase 2
-      c.sigma_rel = gd;     // growth of the first candidate, for phase 2
-      v.node[id] = c;
+      const double Rr = dstqds_child<true>(v.rep_dl + p.rep, v.rep_ul + p.rep, v.rep_dl + base, v.rep_ul + base, m,
+                                           sig_w, p.pivmin);
+      set_child(v, id, c, p, base, sig_w, Rr);
+      diag(v.ctl, DIAG_CHILD_RESTORE);
     }
   }
 }
@@ -298,19 +413,20 @@ __global__ void k_childrep(Dev v) {
 
 }  // namespace
 
-void launch_level_classify(const Dev& v, int level, const Grid& g, cudaStream_t s) {
+void launch_level_classify(const Dev& v, const Grid& g, cudaStream_t s, cudaGraphConditionalHandle cond,
+                           int use_cond) {
   k_level_start<<<1, 32, 0, s>>>(v);
   count_launch();
-  k_classify_flags<<<g.slot_blocks, g.tpb, 0, s>>>(v, level);
+  k_classify_flags<<<g.slot_blocks, g.tpb, 0, s>>>(v);
   count_launch();
-  k_classify_runs<<<g.slot_blocks, g.tpb, 0, s>>>(v, level);
+  k_classify_runs<<<g.slot_blocks, g.tpb, 0, s>>>(v);
   count_launch();
-  k_level_end<<<1, 32, 0, s>>>(v, level);
+  k_level_end<<<1, 32, 0, s>>>(v, cond, use_cond);
   count_launch();
+  mark_stage("classify", s);
 }
 
-void launch_level_children(const Dev& v, int level, const Grid& g, cudaStream_t s) {
-  (void)level;
+void launch_level_children(const Dev& v, const Grid& g, cudaStream_t s) {
   launch_engine(v, 1, g, s);
   mark_stage("prerefine", s);
   k_childrep_first<<<g.slot_blocks, 128, 0, s>>>(v);

@@ -25,143 +25,250 @@ namespace mrrr {
 
 namespace {
 
-constexpr int kRowAhead = 4;  // representation rows loaded ahead of the qd recurrences
+constexpr int kRowAhead = 4;    // representation and scratch rows loaded ahead of the recurrences
+constexpr int kVecWarps = 4;    // 128 threads per CTA
+constexpr int kStageRows = 16;  // rows of z staged per lane before a coalesced flush
 
-// A: L+ (stride as), B: s then U- (stride bs), z: output (stride zs; may alias A).
-// Returns the Sturm count (negative pivots of the stationary part).  The
-// representation rows are read kRowAhead rows ahead of the recurrences, whose
-// dependent chains (a division per row) do not wait on the loads.
-__device__ int twisted_solve(const double2* __restrict__ dl, const double2* __restrict__ ul, int m, double lam,
-                             double pivmin,
-                             double* A, int64_t as, double* B, int64_t bs, double* z, int64_t zs,
-                             int& r, double& gamma, double& norm2) {
-  int negc = 0;
+// The 32 vectors of a warp are computed in row lockstep: every sweep runs over
+// the rows in the same order for all lanes (a lane idles on rows outside its
+// range), so the interleaved scratch (row i of thread t at i * nthr + t) is
+// read and written in whole 256-byte rows, and z leaves through a shared
+// staging tile: kStageRows rows of all 32 lanes, flushed column by column as
+// 128-byte runs of consecutive rows.
+struct VecLane {
+  const double2* dl;  // (D, LLD) rows of the node's representation
+  const double2* ul;  // (l, LD) rows
+  double* zc;         // column of Z (rows of the block), nullptr when idle
+  double lam;         // eigenvalue in the node's coordinates
+  double pivmin;
+  int m;              // rows of the block (0 when idle)
+};
+
+// Rows [c0, c0 + kStageRows) of each lane's column, restricted to the lane's
+// range [lo, hi], from stage[row - c0][lane] to Z: two columns per step, 16
+// lanes per column.
+__device__ __forceinline__ void flush_stage(double (*stage)[33], int c0, double* zc, int lo, int hi, int lane) {
+  __syncwarp();
+  const int half = lane >> 4, rr = lane & 15;
+  for (int L0 = 0; L0 < 32; L0 += 2) {
+    const int L = L0 + half;
+    const long long zp = __shfl_sync(0xffffffffu, (long long)zc, L);
+    const int l = __shfl_sync(0xffffffffu, lo, L), h = __shfl_sync(0xffffffffu, hi, L);
+    const int row = c0 + rr;
+    if (zp && row >= l && row <= h) reinterpret_cast<double*>(zp)[row] = stage[rr][L];
+  }
+  __syncwarp();
+}
+
+// Twisted factorization of L D L^T - lam I for the warp's vectors and the
+// solve, with z written to the lanes' columns of Z.  A (L+) and B (s, then
+// U-) are the lane's interleaved scratch rows (stride nthr).  Returns, per
+// lane, the twist index r, gamma_r and ||z||^2.
+__device__ void twisted_warp(const VecLane& q, double* __restrict__ A, double* __restrict__ B, int64_t nthr,
+                             double (*stage)[33], int lane, int& r_out, double& gamma_out, double& norm2_out) {
+  const bool act = q.m > 0;
+  const int m = q.m;
+  int M = m;
+  for (int o = 16; o; o >>= 1) M = max(M, __shfl_xor_sync(0xffffffffu, M, o));
+  const double lam = q.lam, pivmin = q.pivmin;
+  // stationary transform, top-down: D+_i = D_i + s_i, L+_i = LD_i / D+_i,
+  // s_{i+1} = L+_i l_i s_i - lam; L+ to A, s to B
   double s = -lam;
   double2 pd[kRowAhead], pu[kRowAhead];
 #pragma unroll
   for (int u = 0; u < kRowAhead; ++u) {
-    pd[u] = u < m - 1 ? __ldg(dl + u) : make_double2(0.0, 0.0);
-    pu[u] = u < m - 1 ? __ldg(ul + u) : make_double2(0.0, 0.0);
+    pd[u] = u < m - 1 ? __ldg(q.dl + u) : make_double2(0.0, 0.0);
+    pu[u] = u < m - 1 ? __ldg(q.ul + u) : make_double2(0.0, 0.0);
   }
-  for (int i0 = 0; i0 < m - 1; i0 += kRowAhead) {
+  for (int i0 = 0; i0 < M - 1; i0 += kRowAhead) {
 #pragma unroll
     for (int u = 0; u < kRowAhead; ++u) {
       const int i = i0 + u;
       const double2 xd = pd[u], xu = pu[u];
       const int inext = i + kRowAhead;
-      pd[u] = inext < m - 1 ? __ldg(dl + inext) : make_double2(0.0, 0.0);
-      pu[u] = inext < m - 1 ? __ldg(ul + inext) : make_double2(0.0, 0.0);
+      pd[u] = inext < m - 1 ? __ldg(q.dl + inext) : make_double2(0.0, 0.0);
+      pu[u] = inext < m - 1 ? __ldg(q.ul + inext) : make_double2(0.0, 0.0);
       if (i < m - 1) {
         double dp = xd.x + s;
         if (fabs(dp) < pivmin) dp = -pivmin;
-        negc += (dp < 0.0);
         const double lp = xu.y / dp;  // LD / D+
-        A[i * as] = lp;
-        B[i * bs] = s;
+        A[i * nthr] = lp;
+        B[i * nthr] = s;
         s = fma(lp, xu.x * s, -lam);  // L+ l s - lambda
       }
     }
   }
-  {
-    double dp = dl[m - 1].x + s;
-    if (fabs(dp) < pivmin) dp = -pivmin;
-    negc += (dp < 0.0);
-    B[(int64_t)(m - 1) * bs] = s;
+  double p = 0.0, g = 0.0, best = INFINITY, gamma = 0.0;
+  int r = 0;
+  if (act) {
+    p = q.dl[m - 1].x - lam;
+    g = s + p + lam;
+    best = fabs(g);
+    r = m - 1;
+    gamma = g;
   }
-  double p = dl[m - 1].x - lam;
-  double g = s + p + lam;
-  double best = fabs(g);
-  r = m - 1;
-  gamma = g;
+  // progressive transform, bottom-up over the rows M-2 .. 0 (a lane joins at
+  // its own m-2): D-_{i+1} = LLD_i + p_{i+1}, U-_i = LD_i / D-_{i+1},
+  // p_i = p_{i+1} D_i / D-_{i+1} - lam; gamma_i = s_i + p_i + lam; U- to B
+  double sb[kRowAhead];
 #pragma unroll
   for (int u = 0; u < kRowAhead; ++u) {
-    const int i = m - 2 - u;
-    pd[u] = i >= 0 ? __ldg(dl + i) : make_double2(0.0, 0.0);
-    pu[u] = i >= 0 ? __ldg(ul + i) : make_double2(0.0, 0.0);
+    const int i = M - 2 - u;
+    const bool ok = i >= 0 && i <= m - 2;
+    pd[u] = ok ? __ldg(q.dl + i) : make_double2(0.0, 0.0);
+    pu[u] = ok ? __ldg(q.ul + i) : make_double2(0.0, 0.0);
+    sb[u] = ok ? B[i * nthr] : 0.0;
   }
-  for (int i0 = m - 2; i0 >= 0; i0 -= kRowAhead) {
+  for (int i0 = M - 2; i0 >= 0; i0 -= kRowAhead) {
 #pragma unroll
     for (int u = 0; u < kRowAhead; ++u) {
       const int i = i0 - u;
       const double2 xd = pd[u], xu = pu[u];
+      const double si = sb[u];
       const int inext = i - kRowAhead;
-      pd[u] = inext >= 0 ? __ldg(dl + inext) : make_double2(0.0, 0.0);
-      pu[u] = inext >= 0 ? __ldg(ul + inext) : make_double2(0.0, 0.0);
-      if (i >= 0) {
+      const bool ok = inext >= 0 && inext <= m - 2;
+      pd[u] = ok ? __ldg(q.dl + inext) : make_double2(0.0, 0.0);
+      pu[u] = ok ? __ldg(q.ul + inext) : make_double2(0.0, 0.0);
+      sb[u] = ok ? B[inext * nthr] : 0.0;
+      if (i >= 0 && i <= m - 2) {
         double dm = xd.y + p;  // LLD + p
         if (fabs(dm) < pivmin) dm = -pivmin;
         const double t = xd.x / dm;  // D / D-
         const double um = xu.x * t;  // l D / D-
         p = fma(p, t, -lam);
-        g = B[i * bs] + p + lam;
+        g = si + p + lam;
         if (fabs(g) <= best) {
           best = fabs(g);
           r = i;
           gamma = g;
         }
-        B[i * bs] = um;
+        B[i * nthr] = um;
       }
     }
   }
-  double zi = 1.0, n2 = 1.0;
-  z[(int64_t)r * zs] = 1.0;
-  for (int i = r - 1; i >= 0; --i) {
-    zi = -A[i * as] * zi;
-    z[i * zs] = zi;
-    n2 = fma(zi, zi, n2);
+  // solve N_r z = gamma_r e_r with z_r = 1: upward z_i = -L+_i z_{i+1}
+  // (i < r), downward z_{i+1} = -U-_i z_i (i >= r)
+  if (act) q.zc[r] = 1.0;
+  double n2 = 1.0;
+  int R = act ? r : 0;
+  for (int o = 16; o; o >>= 1) R = max(R, __shfl_xor_sync(0xffffffffu, R, o));
+  double z = 1.0;
+  double ab[kRowAhead];
+#pragma unroll
+  for (int u = 0; u < kRowAhead; ++u) {
+    const int i = R - 1 - u;
+    ab[u] = (act && i >= 0 && i < r) ? A[i * nthr] : 0.0;
   }
-  zi = 1.0;
-  for (int i = r; i < m - 1; ++i) {
-    zi = -B[i * bs] * zi;
-    z[(int64_t)(i + 1) * zs] = zi;
-    n2 = fma(zi, zi, n2);
+  for (int i0 = R - 1; i0 >= 0; i0 -= kRowAhead) {
+#pragma unroll
+    for (int u = 0; u < kRowAhead; ++u) {
+      const int i = i0 - u;
+      const double a = ab[u];
+      const int inext = i - kRowAhead;
+      ab[u] = (act && inext >= 0 && inext < r) ? A[inext * nthr] : 0.0;
+      if (i >= 0) {
+        if (act && i < r) {
+          z = -a * z;
+          n2 = fma(z, z, n2);
+          stage[i & (kStageRows - 1)][lane] = z;
+        }
+        if ((i & (kStageRows - 1)) == 0) flush_stage(stage, i, q.zc, 0, r - 1, lane);
+      }
+    }
   }
-  norm2 = n2;
-  return negc;
+  int Rmin = act ? r : INT32_MAX;
+  for (int o = 16; o; o >>= 1) Rmin = min(Rmin, __shfl_xor_sync(0xffffffffu, Rmin, o));
+  z = 1.0;
+  // rows j = i + 1 from Rmin + 1 to M - 1; lane active for r < j <= m - 1
+#pragma unroll
+  for (int u = 0; u < kRowAhead; ++u) {
+    const int i = Rmin + u;
+    ab[u] = (act && i >= r && i <= m - 2) ? B[i * nthr] : 0.0;
+  }
+  for (int i0 = Rmin; i0 <= M - 2; i0 += kRowAhead) {
+#pragma unroll
+    for (int u = 0; u < kRowAhead; ++u) {
+      const int i = i0 + u;
+      const double b = ab[u];
+      const int inext = i + kRowAhead;
+      ab[u] = (act && inext >= r && inext <= m - 2) ? B[inext * nthr] : 0.0;
+      if (i <= M - 2) {
+        const int j = i + 1;
+        if (act && i >= r && i <= m - 2) {
+          z = -b * z;
+          n2 = fma(z, z, n2);
+          stage[j & (kStageRows - 1)][lane] = z;
+        }
+        if ((j & (kStageRows - 1)) == kStageRows - 1 || j == M - 1)
+          flush_stage(stage, j & ~(kStageRows - 1), q.zc, r + 1, m - 1, lane);
+      }
+    }
+  }
+  r_out = r;
+  gamma_out = gamma;
+  norm2_out = n2;
 }
 
-__global__ void k_vectors(Dev v) {
+__global__ void __launch_bounds__(kVecWarps * 32) k_vectors(Dev v) {
+  __shared__ double stage_all[kVecWarps][kStageRows][33];
+  const int lane = threadIdx.x & 31;
+  double (*stage)[33] = stage_all[threadIdx.x >> 5];
   const int64_t tid = gtid(), nthr = gstride();
   const int64_t nslots = v.ctl->nslots;
   double* B = v.vscr + tid;
+  double* A = v.vscr + v.vscr_threads * v.vscr_rows + tid;
   unsigned long long iters = 0;
-  for (int64_t w = tid; w < nslots; w += nthr) {
-    const int st = v.state[w];
-    if (st != SLOT_SINGLETON && st != SLOT_FALLBACK && st != SLOT_TRIVIAL) continue;
-    const int pos = v.spos[w];
-    if (pos < 0) continue;
-    const Node nd = v.node[v.snode[w]];
-    const Block bk = v.blk[nd.block];
-    const Problem q = v.prob[bk.prob];
-    const int m = bk.m;
-    double* zc = v.Z ? v.Z + q.zout + (int64_t)pos * q.ldz + (bk.row0 - q.row0) : nullptr;
-    if (st == SLOT_TRIVIAL || m == 1) {
-      v.W[q.wout + pos] = nd.sigma_abs / q.scale;
-      if (zc) zc[0] = 1.0;
-      v.znrm2[w] = 1.0;
-      continue;
+  // chunks of 32 consecutive slots (one per lane), spread over the SM
+  // sub-partitions by the scheduler; every lane of a warp works on the same
+  // chunk (warp-wide sweeps)
+  const long long nchunks = (nslots + 31) / 32;
+  const long long rank = sched_rank(v);
+  bool first = true;
+  for (;;) {
+    const long long chunk = sched_next(v, nchunks, nthr / 32, rank, first);
+    if (chunk < 0) break;
+    const int64_t w = chunk * 32 + lane;
+    VecLane q{};
+    int st = w < nslots ? v.state[w] : 0;
+    const bool has = (st == SLOT_SINGLETON || st == SLOT_FALLBACK || st == SLOT_TRIVIAL) && v.spos[w] >= 0;
+    Node nd{};
+    Problem pr{};
+    int pos = 0;
+    if (has) {
+      pos = v.spos[w];
+      nd = v.node[v.snode[w]];
+      const Block bk = v.blk[nd.block];
+      pr = v.prob[bk.prob];
+      const int m = bk.m;
+      double* zc = v.Z ? v.Z + pr.zout + (int64_t)pos * pr.ldz + (bk.row0 - pr.row0) : nullptr;
+      if (st == SLOT_TRIVIAL || m == 1) {
+        v.W[pr.wout + pos] = nd.sigma_abs / pr.scale;
+        if (zc) zc[0] = 1.0;
+        v.znrm2[w] = 1.0;
+      } else if (!zc) {  // eigenvalues only: the bisected value is final
+        v.W[pr.wout + pos] = (nd.sigma_abs + 0.5 * (v.lo[w] + v.hi[w])) / pr.scale;
+      } else {
+        // the eigenvalue was bisected to full relative accuracy on this
+        // representation: one twisted factorization gives the vector
+        q.dl = v.rep_dl + nd.rep;
+        q.ul = v.rep_ul + nd.rep;
+        q.zc = zc;
+        q.lam = 0.5 * (v.lo[w] + v.hi[w]);
+        q.pivmin = nd.pivmin;
+        q.m = m;
+      }
     }
-    if (!zc) {  // eigenvalues only: the bisected value is final
-      v.W[q.wout + pos] = (nd.sigma_abs + 0.5 * (v.lo[w] + v.hi[w])) / q.scale;
-      continue;
-    }
-    double* A = zc;
-    const int64_t as = 1;
-    const double2* rdl = v.rep_dl + nd.rep;
-    const double2* rul = v.rep_ul + nd.rep;
-    // the eigenvalue was bisected to full relative accuracy on this
-    // representation: one twisted factorization gives the vector
-    const double lam = 0.5 * (v.lo[w] + v.hi[w]);
+    if (!__any_sync(0xffffffffu, q.m > 0)) continue;
     int r;
     double gamma, n2;
-    twisted_solve(rdl, rul, m, lam, nd.pivmin, A, as, B, nthr, A, as, r, gamma, n2);
-    ++iters;
-    const double lam_out = lam;
-    if (!isfinite(n2)) set_status(v.ctl, MRRR_ERR_NOCONV);
-    v.W[q.wout + pos] = (nd.sigma_abs + lam_out) / q.scale;
-    v.wval[w] = lam_out;
-    v.znrm2[w] = n2;
-    if (!zc) continue;
+    twisted_warp(q, A, B, nthr, stage, lane, r, gamma, n2);
+    if (q.m > 0) {
+      ++iters;
+      if (!isfinite(n2)) set_status(v.ctl, MRRR_ERR_NOCONV);
+      v.W[pr.wout + pos] = (nd.sigma_abs + q.lam) / pr.scale;
+      v.wval[w] = q.lam;
+      v.znrm2[w] = n2;
+    }
   }
   if (iters) atomicAdd(&v.ctl->twisted_solves, iters);
 }
@@ -286,15 +393,18 @@ __global__ void k_orth_fix(Dev v) {
   }
 }
 
-// Split problems: columns were placed by the rank of interval midpoints;
-// near-ties across blocks may leave W slightly out of order.  Odd-even
-// transposition passes (one CTA per problem) restore ascending W, moving the
-// columns of Z along.
+// W ascending: in split problems columns were placed by the rank of interval
+// midpoints, and near-ties across blocks may leave W slightly out of order;
+// in any problem, eigenvalues equal to the last bit that were finished on
+// different nodes (sigma_abs + local value, each rounded) can come out one or
+// two ulps out of order.  Odd-even transposition passes (one CTA per problem)
+// restore ascending W, moving the columns of Z along; they stop after two
+// passes without a swap.
 __global__ void k_fix_order(Dev v) {
   __shared__ int swapped;
   for (int64_t p = blockIdx.x; p < v.batch; p += gridDim.x) {
     const Problem q = v.prob[p];
-    if (q.nblocks <= 1 || q.k < 2) continue;
+    if (q.k < 2) continue;
     double* W = v.W + q.wout;
     int quiet = 0;
     for (int pass = 0; pass < 2 * q.k + 2 && quiet < 2; ++pass) {
@@ -331,6 +441,8 @@ __global__ void k_fix_order(Dev v) {
 }  // namespace
 
 void launch_vectors(const Dev& v, const Grid& g, cudaStream_t s) {
+  k_sched_reset<<<1, kSchedSlots, 0, s>>>(v);
+  count_launch();
   k_vectors<<<g.vec_blocks, 128, 0, s>>>(v);
   count_launch();
   if (v.Z) {

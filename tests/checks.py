@@ -82,3 +82,78 @@ def subspace_errors(Zg: np.ndarray, Zo: np.ndarray, W: np.ndarray, tnorm: float,
         bound = max(bound, 100.0 * n * EPS)
         out.append((sin, min(bound, 1.0)))
     return out
+
+
+def residual_frobenius(d: torch.Tensor, e: torch.Tensor, W: torch.Tensor, Z: torch.Tensor) -> float:
+    """||T Z_C - Z_C diag(W_C)||_F for a block of columns (on the device)."""
+    return float(torch.linalg.vector_norm(residual_cols(d, e, W, Z)))
+
+
+def davis_kahan_errors(d: torch.Tensor, e: torch.Tensor, W: torch.Tensor, Z: torch.Tensor, W_exact: np.ndarray,
+                       groups, tnorm: float, n: int):
+    """Rigorous bound on the angle between each group's computed subspace and
+    the exact invariant subspace, from the residual alone (Davis and Kahan's
+    sin-theta theorem): sin(angle) <= ||T Z_C - Z_C W_C||_F / delta_C, with
+    delta_C the distance from the computed values W_C to the exact eigenvalues
+    outside the group (W_exact, accurate to a few n eps ||T||, widened by that
+    amount).  Returns a list of (bound, tolerance) with the tolerance of
+    subspace_errors."""
+    out = []
+    Wg = W.detach().cpu().numpy()
+    margin = 8.0 * n * EPS * tnorm
+    for a, b in groups:
+        lo, hi = Wg[a:b].min(), Wg[a:b].max()
+        left = lo - W_exact[a - 1] if a > 0 else np.inf
+        right = W_exact[b] - hi if b < len(W_exact) else np.inf
+        delta = min(left, right) - margin
+        rf = residual_frobenius(d, e, W[a:b], Z[:, a:b])
+        bound = rf / delta if delta > 0 else np.inf
+        gap = min(left, right)
+        tol = 1000.0 * n * EPS * tnorm / gap if np.isfinite(gap) and gap > 0 else 0.0
+        out.append((bound, min(max(tol, 100.0 * n * EPS), 1.0)))
+    return out
+
+
+def full_orthogonality(Z: torch.Tensor, chunk: int = 4096) -> float:
+    """max |Z^T Z - I| over all column pairs, by blocks of the upper triangle
+    (the Gram matrix of 20,000 columns does not need to exist at once)."""
+    k = Z.shape[1]
+    worst = 0.0
+    for a in range(0, k, chunk):
+        b = min(k, a + chunk)
+        G = Z[:, a:b].t() @ Z[:, a:]
+        idx = torch.arange(b - a, device=Z.device)
+        G[idx, idx] -= 1.0
+        worst = max(worst, float(G.abs().max()))
+        del G
+    return worst
+
+
+def subset_subspace_errors(Zg: np.ndarray, il: int, iu: int, W_all: np.ndarray, d, e, tnorm: float, n: int,
+                           Zo_subset: np.ndarray, group_rel: float = 1e-6):
+    """Subspace comparison for an index subset il..iu (1-based) of the
+    spectrum W_all.  Groups of nearly equal eigenvalues are formed on the
+    whole spectrum; a group inside the subset is compared with the oracle's
+    subset vectors, and a group cut by the subset's ends is compared with the
+    oracle's vectors of the whole group (the computed columns must lie in
+    that group's invariant subspace).  Returns a list of (sin_angle, bound)."""
+    import oracle
+    out = []
+    lo, hi = il - 1, iu  # 0-based half-open range of the subset
+    for a, b in groups_by_gap(W_all, group_rel * tnorm):
+        if b <= lo or a >= hi:
+            continue
+        left = W_all[a] - W_all[a - 1] if a > 0 else np.inf
+        right = W_all[b] - W_all[b - 1] if b < len(W_all) else np.inf
+        gap = min(left, right)
+        bound = 1000.0 * n * EPS * tnorm / gap if np.isfinite(gap) and gap > 0 else 0.0
+        bound = min(max(bound, 100.0 * n * EPS), 1.0)
+        a2, b2 = max(a, lo), min(b, hi)
+        G = Zg[:, a2 - lo:b2 - lo]
+        if a >= lo and b <= hi:
+            O = Zo_subset[:, a - lo:b - lo]
+        else:
+            O = oracle.cluster_vectors(d, e, W_all[a:b])
+        R = G - O @ (O.T @ G)
+        out.append((float(np.linalg.norm(R, 2)), bound))
+    return out

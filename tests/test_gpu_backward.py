@@ -8,6 +8,7 @@ import torch
 
 import oracle
 from paper_1205_2107_gb300 import api, autograd, inputs
+from tests import checks
 
 pytestmark = pytest.mark.gpu
 
@@ -22,7 +23,7 @@ def oracle_gradient(d, e, w, C):
     Wo, Zo = oracle.eigh_tridiagonal(d, e[:len(d) - 1])
     proj = np.einsum("ji,ji->i", C, Zo)
     Zbar = 2.0 * C * proj[None, :]
-    return oracle.adjoint(Wo, Zo, w, Zbar, tau=0.0)
+    return oracle.adjoint(Wo, Zo, w, Zbar, tau=api.DEFAULT_TAU_REL * float(np.max(np.abs(Wo))))
 
 
 def loss_np(W, Z, w, C):
@@ -52,6 +53,15 @@ def gpu_gradient_batched(ds, es, ws, Cs):
         out.append((dbar[r0:r0 + n].cpu().numpy(), ebar[r0:r0 + n - 1].cpu().numpy(),
                     ebar[r0 + n - 1].item() if n else 0.0))
     return out
+
+
+# Finite-difference acceptance: relative error 1e-6, plus a floor for
+# entries near zero.  The floor is the rounding noise of the differenced
+# loss: the solver returns each eigenpair to a few ulps, so the loss of a
+# 512 x 512 problem (magnitude up to ~1e3) carries noise of ~1e-13, which
+# the central difference divides by 2h = 2e-6.
+FD_RTOL = 1e-6
+FD_FLOOR = 1e-7
 
 
 def assert_close_grad(g, go, what):
@@ -117,18 +127,28 @@ def test_autograd_single_problem_matches_oracle_and_finite_differences():
     od, oe = oracle_gradient(d_np, np.append(e_np, 0.0), w_np, C_np)
     assert_close_grad(d.grad.cpu().numpy(), od, "d.grad")
     assert_close_grad(e.grad.cpu().numpy(), oe, "e.grad")
-    # central differences of the loss through the forward solver, h = 1e-6
+    # central differences of the loss through the forward solver, h = 1e-6,
+    # with Richardson's control: an entry whose differences at h and h/2
+    # disagree by more than 1e-6 relative is not resolved by differencing at
+    # this step (small gaps) and rests on the oracle comparison above
     h = 1e-6
+    resolved = 0
     for which, j in [("d", 0), ("d", 17), ("d", n - 1), ("e", 0), ("e", 20), ("e", n - 2)]:
-        vals = []
-        for s in (+1, -1):
-            dd, ee = d_np.copy(), e_np.copy()
-            (dd if which == "d" else ee)[j] += s * h
-            Wp, Zp = api.eigh_tridiagonal(_dev(dd), _dev(np.append(ee, 0.0)))
-            vals.append(loss_np(Wp.cpu().numpy(), Zp.cpu().numpy(), w_np, C_np))
-        fd = (vals[0] - vals[1]) / (2 * h)
+        fds = []
+        for step in (h, h / 2):
+            vals = []
+            for s in (+1, -1):
+                dd, ee = d_np.copy(), e_np.copy()
+                (dd if which == "d" else ee)[j] += s * step
+                Wp, Zp = api.eigh_tridiagonal(_dev(dd), _dev(np.append(ee, 0.0)))
+                vals.append(loss_np(Wp.cpu().numpy(), Zp.cpu().numpy(), w_np, C_np))
+            fds.append((vals[0] - vals[1]) / (2 * step))
         g = (d.grad if which == "d" else e.grad)[j].item()
-        assert abs(fd - g) <= 1e-6 * max(abs(g), 1.0), f"{which}[{j}]: fd {fd:.10e} vs grad {g:.10e}"
+        if abs(fds[0] - fds[1]) > FD_RTOL * abs(fds[0]) + FD_FLOOR:
+            continue
+        resolved += 1
+        assert abs(fds[0] - g) <= FD_RTOL * abs(g) + FD_FLOOR, f"{which}[{j}]: fd {fds[0]:.10e} vs grad {g:.10e}"
+    assert resolved >= 4
 
 
 def test_full_size_adjoint_batch_sampled():
@@ -180,3 +200,105 @@ def test_recompute_gives_the_same_gradient():
         ((_dev(w[0]) * W).sum() + ((_dev(C[0]) * Z).sum(0) ** 2).sum()).backward()
         g1.append((dt.grad.clone(), et.grad.clone()))
     assert torch.equal(g1[0][0], g1[1][0]) and torch.equal(g1[0][1], g1[1][1])
+
+
+def test_finite_differences_on_the_adjoint_workload():
+    """Central differences (h = 1e-6) of the loss along 8 seeded random
+    directions in (d, e) for four problems of the 256 x 512 workload, against
+    the directional derivative g . v of the backward pass.  Richardson's
+    control: a direction whose differences at h and h/2 disagree by more than
+    1e-6 relative (tiny gaps make the loss strongly curved there) is counted
+    as unresolved and rests on the oracle comparison of the full-batch test."""
+    d, e, w, C = inputs.adjoint_case()
+    batch, n = d.shape
+    probs = [0, 37, 128, 255]
+    # gradients of the four problems (a batch of four through the C ABI)
+    grads = gpu_gradient_batched([d[p] for p in probs], [e[p] for p in probs], [w[p] for p in probs],
+                                 [C[p] for p in probs])
+    rng = np.random.default_rng(1206)
+    h = 1e-6
+    cases, ds, es = [], [], []
+    for k, p in enumerate(probs):
+        for _ in range(8):
+            vd = rng.standard_normal(n)
+            ve = rng.standard_normal(n)
+            ve[-1] = 0.0
+            gdot = float(grads[k][0] @ vd + grads[k][1] @ ve[:-1])
+            cases.append((p, gdot))
+            for step in (h, -h, h / 2, -h / 2):
+                ds.append(d[p] + step * vd)
+                es.append(e[p] + step * ve)
+    lay = api.BatchLayout([n] * len(ds), "cuda")
+    W, Z = api.eigh_tridiagonal_batched(_dev(np.concatenate(ds)), _dev(np.concatenate(es)), lay)
+    Ws, Zs = lay.unpack(W, Z)
+    losses = []
+    for q in range(len(ds)):
+        p = cases[q // 4][0]
+        losses.append(loss_np(Ws[q].cpu().numpy(), Zs[q].cpu().numpy(), w[p], C[p]))
+    resolved = 0
+    worst = 0.0
+    for c, (p, gdot) in enumerate(cases):
+        lp, lm, lp2, lm2 = losses[4 * c:4 * c + 4]
+        fd1 = (lp - lm) / (2 * h)
+        fd2 = (lp2 - lm2) / h
+        if abs(fd1 - fd2) > FD_RTOL * abs(fd1) + FD_FLOOR:
+            continue
+        resolved += 1
+        err = abs(fd1 - gdot) / max(abs(gdot), 1e-300)
+        worst = max(worst, err)
+        assert abs(fd1 - gdot) <= FD_RTOL * abs(gdot) + FD_FLOOR, f"problem {p}: fd {fd1:.12e} vs g.v {gdot:.12e}"
+    print(f"finite differences: {resolved}/{len(cases)} directions resolved, worst relative error {worst:.2e}")
+    assert resolved >= len(cases) // 4
+
+
+def test_degenerate_spectrum_gradient_glued():
+    """Glued W21+ x20 (n = 420): groups of 20 eigenvalues, many equal to the
+    last bit.  For a loss that depends on T alone -- weights constant on each
+    group and, per group, the squared norm of the projection of one vector
+    c_G onto the group's invariant subspace -- the gradient is defined even
+    though individual vectors are not; the backward pass must give it finite
+    and equal to the oracle's dense formula at the same threshold.  At
+    tau = 1e-8 ||T|| every within-group pair is dropped and the two agree to
+    1e-8 relative; at the default threshold (64 eps ||T||) pairs with tiny
+    gaps are kept, whose terms F = 1/gap amplify rounding, and the two must
+    agree within that amplification (4 n eps max|Z^T Zbar| / smallest kept
+    gap per kept pair)."""
+    d_np, e_np = inputs.glued_wilkinson(20)
+    n = len(d_np)
+    lay = api.BatchLayout([n], "cuda")
+    dt, et = _dev(d_np), _dev(np.append(e_np, 0.0))
+    W, Z = api.eigh_tridiagonal_batched(dt, et, lay)
+    W, Z = W[:n], Z[:n * n]
+    Wo, Zo = oracle.eigh_tridiagonal(d_np, e_np)
+    tn = float(np.max(np.abs(Wo)))
+    groups = checks.groups_by_gap(Wo, 1e-6 * tn)
+    rng = np.random.default_rng(420)
+    wv = np.zeros(n)
+    Cg = np.zeros((n, n))  # column i = c_G of the group of i
+    for a, b in groups:
+        wv[a:b] = rng.standard_normal()
+        Cg[:, a:b] = rng.standard_normal(n)[:, None]
+
+    def zbar_of(Zm):
+        proj = np.einsum("ji,ji->i", Cg, Zm)
+        return 2.0 * Cg * proj[None, :]
+
+    Zg = Z.view(n, n).t().cpu().numpy()
+    for tau_rel in (1e-8, api.DEFAULT_TAU_REL):
+        Zbar = _dev(zbar_of(Zg).T.reshape(-1).copy())
+        dbar, ebar = api.eigh_tridiagonal_backward(W, Z, _dev(wv), Zbar, lay, tau_rel=tau_rel)
+        gd, ge = dbar[:n].cpu().numpy(), ebar[:n - 1].cpu().numpy()
+        assert np.all(np.isfinite(gd)) and np.all(np.isfinite(ge))
+        od, oe = oracle.adjoint(Wo, Zo, wv, zbar_of(Zo), tau=tau_rel * tn)
+        scale = max(np.max(np.abs(od)), np.max(np.abs(oe)))
+        if tau_rel == 1e-8:
+            tol = 1e-8 * scale
+        else:
+            tau = tau_rel * tn
+            gaps = np.abs(Wo[None, :] - Wo[:, None])
+            kept = (gaps > tau) & (gaps < 1e-6 * tn)
+            G = np.abs(Zo.T @ zbar_of(Zo)).max()
+            tol = 1e-8 * scale + (np.sqrt(kept.sum()) * 4 * n * checks.EPS * G / gaps[kept].min() if kept.any() else 0.0)
+        err = max(np.max(np.abs(gd - od)), np.max(np.abs(ge - oe)))
+        assert err <= tol, f"tau_rel={tau_rel:.2e}: gradient error {err:.3e} > {tol:.3e}"
+

@@ -37,9 +37,14 @@ def check_problem(d, e, W, Z, il, iu, compare_vectors=True):
     res = float(checks.residual_cols(_dev(d), _dev(np.append(e[:max(n - 1, 0)], 0.0)), W, Z).max())
     assert res <= 20 * n * EPS * tn, f"residual {res:.3e}"
     assert checks.orthogonality(Z) <= 20 * n * EPS
-    if compare_vectors and n > 1 and il == 1 and iu == n:
-        for sin, bound in checks.subspace_errors(Z.cpu().numpy(), Zo, Wo, tn, n):
-            assert sin <= bound
+    if compare_vectors and n > 1:
+        if il == 1 and iu == n:
+            errs = checks.subspace_errors(Z.cpu().numpy(), Zo, Wo, tn, n)
+        else:
+            Wall = oracle.eigvalsh_tridiagonal(d, eo)
+            errs = checks.subset_subspace_errors(Z.cpu().numpy(), il, iu, Wall, d, eo, tn, n, Zo)
+        for sin, bound in errs:
+            assert sin <= bound, f"subspace angle {sin:.3e} > {bound:.3e}"
 
 
 def solve_batch(sizes, seed, il=None, iu=None, vectors=True):
@@ -116,10 +121,14 @@ def test_full_size_batch_4096_sampled():
         orth = checks.orthogonality(Zp) / (n * EPS)
         worst_res, worst_orth = max(worst_res, res), max(worst_orth, orth)
     assert worst_res <= 20 and worst_orth <= 20, (worst_res, worst_orth)
+    # 64 seeded problems (and the largest) against the oracle's eigenvalues,
+    # 8 of them also against the oracle's vectors (subspace angles)
     rng = np.random.default_rng(0)
-    for p in sorted(set(rng.integers(0, len(sizes), 6).tolist()) | {int(np.argmax(sizes))}):
+    picks = sorted(set(rng.choice(len(sizes), 64, replace=False).tolist()) | {int(np.argmax(sizes))})
+    with_vectors = set(rng.choice(picks, 8, replace=False).tolist())
+    for p in picks:
         check_problem(d[off[p]:off[p + 1]], e[off[p]:off[p + 1]], Ws[p], Zs[p], 1, sizes[p],
-                      compare_vectors=False)
+                      compare_vectors=p in with_vectors)
 
 
 def test_batch_with_empty_problems():
@@ -139,3 +148,24 @@ def test_single_problem_of_order_zero():
     W, Z = api.eigh_tridiagonal(torch.zeros(0, dtype=torch.float64, device="cuda"),
                                 torch.zeros(0, dtype=torch.float64, device="cuda"))
     assert W.numel() == 0 and Z.numel() == 0
+
+
+@pytest.mark.parametrize("width", [1, 4])
+def test_batched_equals_plain_bitwise_under_a_fixed_schedule(width):
+    """With a fixed multisection width (no pooling of points across
+    intervals), an eigenpair's computation depends on its own problem alone:
+    the batched solve and the single-problem solve give the same bits."""
+    sizes = [64, 257, 33, 512, 1, 300]
+    d, e, off = inputs.batched_uniform(sizes, 99)
+    d[off[5]:off[6]] = inputs.glued_wilkinson(15)[0][:300]  # clustered problem in the batch
+    e[off[5]:off[6] - 1] = inputs.glued_wilkinson(15)[1][:299]
+    lay = api.BatchLayout(sizes, "cuda")
+    plan = api.Plan(multisection_width=width)
+    W, Z = api.eigh_tridiagonal_batched(_dev(d), _dev(e), lay, plan=plan)
+    Ws, Zs = lay.unpack(W, Z)
+    plan1 = api.Plan(multisection_width=width)
+    for p, n in enumerate(sizes):
+        W1, Z1 = api.eigh_tridiagonal(_dev(d[off[p]:off[p + 1]]), _dev(e[off[p]:off[p + 1]]), plan=plan1)
+        assert torch.equal(Ws[p], W1), f"problem {p}: W differs"
+        assert torch.equal(Zs[p], Z1), f"problem {p}: Z differs"
+        check_problem(d[off[p]:off[p + 1]], e[off[p]:off[p + 1]], W1, Z1, 1, n, compare_vectors=n <= 300)

@@ -1,9 +1,9 @@
 """GPU parity at the large single-problem size: n = 50,000, d iid U[0,1],
 e iid U[0, 1e-2] (Z = 20 GB in HBM), all eigenpairs and the index subset
 25001..30000.  The oracle gives all eigenvalues (bisection); vectors are
-checked by residual, by orthogonality against sampled columns and within a
-band of neighbours (where loss of orthogonality concentrates), and in full
-for the subset."""
+checked by residual, by orthogonality of every column against 1,024 seeded
+columns and against its 256 neighbours on each side (where loss of
+orthogonality concentrates), and in full for the subset."""
 import numpy as np
 import pytest
 import torch
@@ -38,9 +38,12 @@ def test_large_all_eigenpairs_sampled(large):
     for a in range(0, n, 5000):  # residual of every column, in slices of 5000
         res = max(res, float(checks.residual_cols(dt, et, W[a:a + 5000], Z[:, a:a + 5000]).max()))
     assert res <= 20 * n * EPS * tn, f"residual {res:.3e}"
-    cols = torch.as_tensor(np.random.default_rng(1).choice(n, 256, replace=False), device="cuda")
+    # all columns against a seeded sample of 1,024 columns, and every column
+    # against its 256 neighbours on each side in eigenvalue order (where loss
+    # of orthogonality concentrates)
+    cols = torch.as_tensor(np.random.default_rng(1).choice(n, 1024, replace=False), device="cuda")
     assert checks.orthogonality(Z, cols) <= 20 * n * EPS
-    assert checks.band_orthogonality(Z, width=32) <= 20 * n * EPS
+    assert checks.band_orthogonality(Z, width=256) <= 20 * n * EPS
     del Z
 
 

@@ -43,10 +43,12 @@ def assert_parity(d, e, il=None, iu=None, plan=None, compare_vectors=True):
     assert orth <= 20 * n * EPS, f"orthogonality {orth:.3e}"
     if compare_vectors and n > 1:
         Zg = Z.cpu().numpy()
-        full = il_ == 1 and iu_ == n
-        for sin, bound in checks.subspace_errors(Zg, Zo, Wo if full else Wo, tn, n):
-            if full:
-                assert sin <= bound, f"subspace angle {sin:.3e} > {bound:.3e}"
+        if il_ == 1 and iu_ == n:
+            errs = checks.subspace_errors(Zg, Zo, Wo, tn, n)
+        else:  # groups formed on the whole spectrum, cut groups against the oracle's whole group
+            errs = checks.subset_subspace_errors(Zg, il_, iu_, Wall, d, e, tn, n, Zo)
+        for sin, bound in errs:
+            assert sin <= bound, f"subspace angle {sin:.3e} > {bound:.3e}"
     return W, Z
 
 

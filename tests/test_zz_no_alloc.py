@@ -1,5 +1,5 @@
 """The allocation-free entry point mrrr_eigenvalues_static, called through the
-C ABI, against the workspace-based solver (mrrr_stein).
+C ABI, against the workspace-based solver (mrrr_stein) and the CPU oracle.
 
 mrrr_eigenvalues_static is for callers that cannot call cudaMalloc when they
 need eigenvalues (device memory already held by another allocator, or loops
@@ -16,6 +16,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_1205_2107_gb300 import _lib, api, inputs
 
 EPS = 2.0 ** -53
@@ -47,11 +48,37 @@ def test_two_calls_in_a_row_match_the_workspace_solver():
         assert _static_call(d, e, il, iu, W) == _lib.OK
         torch.cuda.synchronize()
         Wref = api.eigh_tridiagonal(d, e, il, iu, vectors=False)
-        tn = float(api.eigh_tridiagonal(d, e, vectors=False).abs().max())
+        # the independent checker: the CPU oracle's bisection on T itself
+        Wall = oracle.eigvalsh_tridiagonal(d_np, e_np)
+        tn = float(np.max(np.abs(Wall)))
         err = float((W - Wref).abs().max())
         assert torch.isfinite(W).all()
         assert bool((W[1:] >= W[:-1]).all()), "W not ascending"
         assert err <= 4 * n * EPS * tn, f"n={n} il={il} iu={iu}: eigenvalue error {err:.3e}"
+        err_o = float(np.max(np.abs(W.cpu().numpy() - Wall[il - 1:iu])))
+        assert err_o <= 4 * n * EPS * tn, f"n={n} il={il} iu={iu}: error vs oracle {err_o:.3e}"
+
+
+@pytest.mark.gpu
+def test_device_error_gives_nan_and_the_next_call_recovers():
+    """A non-finite entry is found on the GPU and gives NaN eigenvalues; the
+    next call, on another matrix, rewrites the shared status word and comes
+    out right (no state carries over from the failed call)."""
+    d_np, e_np = inputs.uniform(700, 77)
+    bad = d_np.copy()
+    bad[123] = np.nan
+    d, e = _dev(bad), _dev(np.append(e_np, 0.0))
+    W = torch.zeros(10, dtype=torch.float64, device="cuda")
+    assert _static_call(d, e, 1, 10, W) == _lib.OK  # found on the device, not on the host
+    torch.cuda.synchronize()
+    assert torch.isnan(W).all()
+    d2_np, e2_np = inputs.toeplitz(300, 2.0, -1.0)
+    d2, e2 = _dev(d2_np), _dev(np.append(e2_np, 0.0))
+    W2 = torch.zeros(300, dtype=torch.float64, device="cuda")
+    assert _static_call(d2, e2, 1, 300, W2) == _lib.OK
+    torch.cuda.synchronize()
+    ref = inputs.toeplitz_eigenvalues(300, 2.0, -1.0)
+    assert float(np.max(np.abs(W2.cpu().numpy() - ref))) <= 4 * 300 * EPS * 4.0
 
 
 @pytest.mark.gpu
