@@ -53,7 +53,9 @@ typedef enum mrrr_status {
   MRRR_ERR_TIMEOUT = 6,    /* reserved (bounded device waits); no kernel of
                               this version waits on another                */
   MRRR_ERR_CUDA = 7,       /* a CUDA runtime call failed                   */
-  MRRR_ERR_NOTIMPL = 8     /* option combination not implemented           */
+  MRRR_ERR_NOTIMPL = 8,    /* option combination not implemented           */
+  MRRR_ERR_MARGIN = 9      /* mrrr_stein_slice: a cluster reaching into the slice
+                              extends past the margin (call again with a larger one) */
 } mrrr_status;
 
 /* Tunables.  Zero-initialise and call mrrr_options_default(); fields left at
@@ -166,6 +168,48 @@ mrrr_status mrrr_workspace_size(const mrrr_plan* plan, int batch, int64_t n_tota
 mrrr_status mrrr_stein(mrrr_plan* plan, int n, const double* d, const double* e, int il, int iu,
                        double* W, double* Z, int64_t ldz, void* workspace, size_t ws_bytes,
                        mrrr_stream stream);
+
+/*
+ * mrrr_slice_range: the index range a..b (1-based, inclusive) of slice
+ * `slice` (0-based) when il..iu is cut into nslices equal contiguous slices:
+ * a = il + floor(slice k / nslices), b = il + floor((slice+1) k / nslices) - 1
+ * with k = iu - il + 1 (the paper's static division of the eigenpairs among
+ * processes, Sec. 3.1.2).  Host only.  MRRR_ERR_ARG for an empty range, a
+ * slice out of range or more slices than indices.
+ */
+mrrr_status mrrr_slice_range(int il, int iu, int nslices, int slice, int* a, int* b);
+
+/*
+ * mrrr_stein_slice: the eigenpairs of slice `slice` of nslices equal slices
+ * of il..iu (mrrr_slice_range), computed so that the slices, each on its own
+ * GPU or one after the other, together give the solution of il..iu: their
+ * columns are mutually orthogonal as those of one solve are.  The paper's
+ * PMRRR divides the wanted eigenpairs statically among processes, computes
+ * the root representation redundantly in each, and lets processes that hold
+ * members of one cluster cooperate on it (Sec. 3.1.2).  Here each slice
+ * computes its indices plus `margin` more on each side (the root
+ * representation redundantly, its shift on the side that il..iu as a whole
+ * chooses), and a cluster that reaches across a slice boundary is computed
+ * whole, identically, by both slices, each returning its own columns: no
+ * data moves between slices.  For that every eigenpair must come out the
+ * same whichever slice computes it, so a slice call uses a fixed schedule
+ * (the plan's multisection_width, 4 when it is 0), and skips the neighbour
+ * orthogonality safeguard.
+ *   il, iu, nslices, slice   as in mrrr_slice_range
+ *   margin     indices computed beyond each end of the slice (>= 1); when a
+ *              cluster holding returned indices reaches past it the device
+ *              status is MRRR_ERR_MARGIN: call again with a larger margin
+ *   W, Z       device, W[b-a+1] and an n x (b-a+1) column-major Z (ldz >= n)
+ *              for the slice's indices a..b (Z may be NULL)
+ *   workspace  ws_bytes >= mrrr_workspace_size(plan, 1, n,
+ *              min(n, b+margin) - max(1, a-margin) + 1, n)
+ * W is ascending within a slice; across a slice boundary, eigenvalues equal
+ * to the last bit may come out one ulp apart in either order.  Other
+ * arguments, errors and synchronisation as in mrrr_stein.
+ */
+mrrr_status mrrr_stein_slice(mrrr_plan* plan, int n, const double* d, const double* e, int il, int iu, int nslices,
+                             int slice, int margin, double* W, double* Z, int64_t ldz, void* workspace,
+                             size_t ws_bytes, mrrr_stream stream);
 
 /*
  * mrrr_stein_batched: many independent problems in one set of launches.

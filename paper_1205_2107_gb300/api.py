@@ -147,6 +147,9 @@ def _run_with_retry(plan: Plan, call, where: str, check: bool):
             return None
         info = plan.info()
         st = info["status"]
+        if st == _lib.ERR_MARGIN and hasattr(call, "grow_margin") and attempt < 3:
+            call.grow_margin()
+            continue
         if st == _lib.ERR_QUEUE and attempt < 3:
             need_rows = int(info["pool_rows_used"] * 2) + 1024
             need_nodes = int(max(info["nodes"], 16) * 2)
@@ -199,6 +202,61 @@ def eigh_tridiagonal(d: torch.Tensor, e: torch.Tensor, il: int | None = None, iu
     Zt = torch.empty((k, n), dtype=_F64, device=d.device) if vectors else None
     _run_with_retry(plan, _SteinCall(plan, n, d, e, il, iu, W, Zt), "mrrr_stein", check)
     return (W, Zt.t()) if vectors else W
+
+
+def slice_range(il: int, iu: int, nslices: int, slice_: int) -> tuple[int, int]:
+    """Indices a..b (1-based, inclusive) of slice ``slice_`` of ``nslices``
+    equal contiguous slices of il..iu (mrrr_slice_range; host only)."""
+    a, b = ctypes.c_int(0), ctypes.c_int(0)
+    _lib.check(_lib.load().mrrr_slice_range(int(il), int(iu), int(nslices), int(slice_), ctypes.byref(a),
+                                            ctypes.byref(b)), "mrrr_slice_range")
+    return int(a.value), int(b.value)
+
+
+class _SliceCall:
+    def __init__(self, plan, n, d, e, il, iu, nslices, slice_, margin, W, Zt):
+        self.__dict__.update(locals())
+        self.a, self.b = slice_range(il, iu, nslices, slice_)
+
+    def grow_margin(self):
+        self.margin *= 4
+
+    def ws_bytes(self):
+        lo, hi = max(1, self.a - self.margin), min(self.n, self.b + self.margin)
+        return self.plan.workspace_size(1, self.n, hi - lo + 1, self.n)
+
+    def __call__(self, ws, ws_bytes):
+        return _lib.load().mrrr_stein_slice(
+            self.plan.handle, self.n, _ptr(self.d), _ptr(self.e if self.n > 1 else self.d), self.il, self.iu,
+            self.nslices, self.slice_, self.margin, _ptr(self.W), _ptr(self.Zt), self.n, _ptr(ws), ws_bytes,
+            _stream_handle(self.d.device))
+
+
+def eigh_tridiagonal_slice(d: torch.Tensor, e: torch.Tensor, il: int | None, iu: int | None, nslices: int,
+                           slice_: int, *, margin: int = 32, vectors: bool = True, plan: Plan | None = None,
+                           check: bool = True):
+    """Eigenpairs of slice ``slice_`` of ``nslices`` equal slices of il..iu
+    (mrrr_stein_slice): (W, Z, (a, b)) for the slice's indices a..b.  The
+    slices of one range, solved separately (on different GPUs or one after
+    the other), together form the solution of the range.  A cluster reaching
+    past ``margin`` makes the call grow the margin fourfold and solve again
+    (only when ``check``)."""
+    d = _check_input(d, "d")
+    n = d.numel()
+    e = _check_input(e, "e") if n > 1 else d
+    il = 1 if il is None else int(il)
+    iu = n if iu is None else int(iu)
+    if n == 0:
+        W = torch.empty(0, dtype=_F64, device=d.device)
+        return (W, torch.empty((0, 0), dtype=_F64, device=d.device), (1, 0)) if vectors else (W, (1, 0))
+    a, b = slice_range(il, iu, nslices, slice_)
+    k = b - a + 1
+    plan = plan or default_plan(d.device)
+    W = torch.empty(k, dtype=_F64, device=d.device)
+    Zt = torch.empty((k, n), dtype=_F64, device=d.device) if vectors else None
+    call = _SliceCall(plan, n, d, e, il, iu, nslices, slice_, int(margin), W, Zt)
+    _run_with_retry(plan, call, "mrrr_stein_slice", check)
+    return (W, Zt.t(), (a, b)) if vectors else (W, (a, b))
 
 
 class _BatchedCall:

@@ -26,7 +26,8 @@ struct GraphKey {
 static bool same_key(const GraphKey& x, const GraphKey& y) {
   const mrrr::ProblemArgs &a = x.a, &b = y.a;
   return a.batch == b.batch && a.d_off == b.d_off && a.il == b.il && a.iu == b.iu && a.w_off == b.w_off &&
-         a.z_off == b.z_off && a.n == b.n && a.il1 == b.il1 && a.iu1 == b.iu1 && a.ldz == b.ldz && x.d == y.d &&
+         a.z_off == b.z_off && a.n == b.n && a.il1 == b.il1 && a.iu1 == b.iu1 && a.ldz == b.ldz &&
+         a.slice == b.slice && a.ol1 == b.ol1 && a.ou1 == b.ou1 && x.d == y.d &&
          x.e == y.e && x.ws == y.ws && x.W == y.W && x.Z == y.Z && x.n_total == y.n_total &&
          x.k_total == y.k_total && x.n_max == y.n_max && x.ws_bytes == y.ws_bytes && x.opt_version == y.opt_version;
 }
@@ -153,6 +154,7 @@ void StageTimer::finish() {
 namespace {
 
 constexpr size_t kAlign = 256;
+constexpr int kSliceWidth = 4;  // multisection width of slice calls unless the options fix one
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
@@ -297,6 +299,18 @@ Grid make_grid(const mrrr_plan* p, int64_t max_slots, int n_max) {
 
 mrrr_status cuda_status(cudaError_t e) { return e == cudaSuccess ? MRRR_OK : MRRR_ERR_CUDA; }
 
+// A slice of an index range (mrrr_stein_slice) must come out the same in
+// every slice that computes it: a fixed multisection width (no pooling of
+// points, whose runs depend on the list), the root shift on the side the
+// whole range decides (root_side set by the entry point), and no neighbour
+// orthogonality safeguard (its runs depend on which columns the call holds).
+void slice_overrides(const mrrr_plan* p, const ProblemArgs& a, Dev& v) {
+  if (!a.slice) return;
+  v.fixed_width = p->opt.multisection_width > 0 ? p->opt.multisection_width : kSliceWidth;
+  v.root_side = a.slice;  // 1 left, 2 right (set by mrrr_stein_slice)
+  v.no_orth_fix = 1;
+}
+
 // One solve enqueued on s.  device_levels: every level up to max_depth is
 // enqueued without host synchronisation and the level kernels return at
 // once after the tree is complete; otherwise the host reads the new-cluster
@@ -307,6 +321,7 @@ mrrr_status solve(mrrr_plan* p, const ProblemArgs& a, const double* d, const dou
   Layout L = make_layout(p, a.batch, n_total, k_total, n_max);
   if (!ws || ws_bytes < L.total) return MRRR_ERR_WORKSPACE;
   Dev v = make_dev(p, L, ws, a.batch, d, e, W, Z);
+  slice_overrides(p, a, v);
   Grid g = make_grid(p, L.max_slots, n_max);
   p->last_ws = ws;
   p->last_graph = false;
@@ -367,6 +382,7 @@ mrrr_status capture_conditional(mrrr_plan* p, const ProblemArgs& a, const double
   *out = nullptr;
   Layout L = make_layout(p, a.batch, n_total, k_total, n_max);
   Dev v = make_dev(p, L, ws, a.batch, d, e, W, Z);
+  slice_overrides(p, a, v);
   Grid g = make_grid(p, L.max_slots, n_max);
   cudaStream_t cs = p->cap_stream;
   const cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
@@ -612,6 +628,39 @@ mrrr_status mrrr_stein(mrrr_plan* plan, int n, const double* d, const double* e,
                   static_cast<cudaStream_t>(stream));
 }
 
+mrrr_status mrrr_slice_range(int il, int iu, int nslices, int slice, int* a, int* b) {
+  if (!a || !b || il < 1 || iu < il || nslices < 1 || slice < 0 || slice >= nslices || nslices > iu - il + 1)
+    return MRRR_ERR_ARG;
+  const int64_t k = (int64_t)iu - il + 1;
+  *a = il + (int)((int64_t)slice * k / nslices);
+  *b = il + (int)((int64_t)(slice + 1) * k / nslices) - 1;
+  return MRRR_OK;
+}
+
+mrrr_status mrrr_stein_slice(mrrr_plan* plan, int n, const double* d, const double* e, int il, int iu, int nslices,
+                             int slice, int margin, double* W, double* Z, int64_t ldz, void* workspace,
+                             size_t ws_bytes, mrrr_stream stream) {
+  if (!plan || n < 0) return MRRR_ERR_ARG;
+  if (n == 0) return MRRR_OK;
+  int a = 0, b = 0;
+  if (!d || (n > 1 && !e) || !W || il < 1 || iu > n || il > iu || (Z && ldz < n) || margin < 1 ||
+      mrrr_slice_range(il, iu, nslices, slice, &a, &b) != MRRR_OK)
+    return MRRR_ERR_ARG;
+  ProblemArgs pa{};
+  pa.batch = 1;
+  pa.n = n;
+  pa.il1 = std::max(1, a - margin);
+  pa.iu1 = std::min(n, b + margin);
+  pa.ol1 = a;
+  pa.ou1 = b;
+  // the root shift on the side the whole range il..iu chooses, for every slice
+  pa.slice = (il + iu) <= (n + 1) ? 1 : 2;
+  pa.ldz = Z ? ldz : n;
+  const double* ee = (n > 1) ? e : d;
+  return dispatch(plan, pa, d, ee, W, Z, n, (int64_t)(pa.iu1 - pa.il1 + 1), n, workspace, ws_bytes,
+                  static_cast<cudaStream_t>(stream));
+}
+
 mrrr_status mrrr_stein_batched(mrrr_plan* plan, int batch, const int64_t* d_off, const double* d, const double* e,
                                const int* il, const int* iu, double* W, const int64_t* w_off, double* Z,
                                const int64_t* z_off, int64_t n_total, int64_t k_total, int n_max, void* workspace,
@@ -774,6 +823,7 @@ const char* mrrr_status_string(mrrr_status s) {
     case MRRR_ERR_TIMEOUT: return "bounded device wait gave up";
     case MRRR_ERR_CUDA: return "CUDA runtime error";
     case MRRR_ERR_NOTIMPL: return "not implemented";
+    case MRRR_ERR_MARGIN: return "slice margin too small for a cluster at the slice boundary";
   }
   return "unknown status";
 }

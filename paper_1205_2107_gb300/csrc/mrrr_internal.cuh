@@ -37,7 +37,10 @@ __device__ __forceinline__ bool slot_final(int st) {
 struct Problem {
   int64_t row0;   // first row in the packed d / e
   int n;
-  int il, iu;     // requested range (1-based, inclusive)
+  int il, iu;     // range of eigenvalues computed (1-based, inclusive)
+  int ol, ou;     // range returned (within il..iu; equal to it except for a slice)
+  int slice;      // a slice of a larger index range (mrrr_stein_slice)
+  int pad_;
   int nblocks;
   int block0;     // first block index
   int k;          // iu - il + 1
@@ -180,6 +183,7 @@ struct Dev {
   int engine_ctas;      // engine CTAs per SM (1 or 2)
   double width_scale;   // multiplies the resident lanes when choosing the multisection width
   int fixed_width;      // 0: width from the list length, brackets pooled; else fixed width, no pooling
+  int no_orth_fix;      // skip the neighbour orthogonality safeguard (slices)
   int root_side;        // 0 nearer the wanted range, 1 left, 2 right
 };
 

@@ -17,8 +17,10 @@ struct ProblemArgs {
   const int64_t* w_off;
   const int64_t* z_off;
   int n;                 // single-problem scalars
-  int il1, iu1;
+  int il1, iu1;          //   range computed
   int64_t ldz;
+  int slice;             //   a slice call: returns ol1..ou1 of the computed range
+  int ol1, ou1;
 };
 
 // The solver's stages, in launch order (names of the per-stage profile).

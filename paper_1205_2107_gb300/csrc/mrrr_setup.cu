@@ -63,10 +63,22 @@ __global__ void k_problems(Dev v, ProblemArgs a) {
       set_status(v.ctl, MRRR_ERR_ARG);
       n = 0;
     }
+    int ol = il, ou = iu;
+    if (a.d_off == nullptr && a.slice) {
+      ol = a.ol1;
+      ou = a.ou1;
+      if (n && (ol < il || ou > iu || ol > ou)) {
+        set_status(v.ctl, MRRR_ERR_ARG);
+        n = 0;
+      }
+    }
     q.n = n;
     q.il = n ? il : 1;
     q.iu = n ? iu : 0;
-    q.k = n ? iu - il + 1 : 0;
+    q.ol = n ? ol : 1;
+    q.ou = n ? ou : 0;
+    q.slice = a.d_off == nullptr ? a.slice : 0;
+    q.k = n ? ou - ol + 1 : 0;
     q.scale = 1.0;
     v.prob[p] = q;
   }
@@ -251,7 +263,7 @@ __global__ void k_blocks(Dev v) {
         int64_t w = q.slot0 + (j - js);
         v.snode[w] = b;
         v.sj[w] = j;
-        v.spos[w] = (j >= q.il && j <= q.iu) ? j - q.il : -1;
+        v.spos[w] = (j >= q.ol && j <= q.ou) ? j - q.ol : -1;
         v.state[w] = q.n == 1 ? SLOT_TRIVIAL : SLOT_ACTIVE;
       }
     }
@@ -434,7 +446,7 @@ __global__ void k_rank(Dev v) {
       double ku = slot_key(v, u);
       rank += (ku < key) || (ku == key && u < w);
     }
-    int64_t pos = rank - (q.il - 1);
+    int64_t pos = rank - (q.ol - 1);
     v.spos[w] = (pos >= 0 && pos < q.k) ? (int)pos : -1;
   }
 }

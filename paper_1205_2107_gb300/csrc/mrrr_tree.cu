@@ -84,6 +84,18 @@ __global__ void k_classify_runs(Dev v) {
     while (e < nd.last && !v.bflag[e]) ++e;
     const double gl = (w == nd.first) ? nd.gapl : v.lo[w] - v.hi[w - 1];
     const double gr = (e == nd.last) ? nd.gapr : v.lo[e + 1] - v.hi[e];
+    if (level == 0) {
+      // a slice computes its indices plus a margin on each side; a root
+      // cluster that holds returned indices must lie inside the computed
+      // range (not touch an end that is not an end of the spectrum), or its
+      // neighbouring slice may group it differently
+      const Block& bk = v.blk[nd.block];
+      if (v.prob[bk.prob].slice && ((w == nd.first && bk.js > 1) || (e == nd.last && bk.je < bk.m))) {
+        bool returned = false;
+        for (int64_t t = w; t <= e && !returned; ++t) returned = v.spos[t] >= 0;
+        if (returned) set_status(v.ctl, MRRR_ERR_MARGIN);
+      }
+    }
     if (e == w) {
       v.state[w] = SLOT_SINGLETON;
       v.gap[w] = fmin(gl, gr);

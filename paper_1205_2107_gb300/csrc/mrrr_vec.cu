@@ -448,10 +448,12 @@ void launch_vectors(const Dev& v, const Grid& g, cudaStream_t s) {
   if (v.Z) {
     k_normalize<<<g.nsm * 16, 256, 0, s>>>(v);
     count_launch();
-    k_orth_links<<<g.nsm * 16, 256, 0, s>>>(v);
-    count_launch();
-    k_orth_fix<<<g.nsm * 4, 128, 0, s>>>(v);
-    count_launch();
+    if (!v.no_orth_fix) {
+      k_orth_links<<<g.nsm * 16, 256, 0, s>>>(v);
+      count_launch();
+      k_orth_fix<<<g.nsm * 4, 128, 0, s>>>(v);
+      count_launch();
+    }
   }
   k_fix_order<<<g.nsm, 256, 0, s>>>(v);
   count_launch();
