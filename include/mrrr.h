@@ -54,8 +54,10 @@ typedef enum mrrr_status {
                               this version waits on another                */
   MRRR_ERR_CUDA = 7,       /* a CUDA runtime call failed                   */
   MRRR_ERR_NOTIMPL = 8,    /* option combination not implemented           */
-  MRRR_ERR_MARGIN = 9      /* mrrr_stein_slice: a cluster reaching into the slice
+  MRRR_ERR_MARGIN = 9,     /* mrrr_stein_slice: a cluster reaching into the slice
                               extends past the margin (call again with a larger one) */
+  MRRR_ERR_NOTSPD = 10     /* Cholesky factorization: the matrix is not positive
+                              definite (a pivot is not positive) */
 } mrrr_status;
 
 /* Tunables.  Zero-initialise and call mrrr_options_default(); fields left at
@@ -332,6 +334,95 @@ mrrr_status mrrr_backward_workspace_size(const mrrr_plan* plan, int batch, int64
 #define MRRR_STATIC_MAX_N 8192
 mrrr_status mrrr_eigenvalues_static(int n, const double* d, const double* e, int il, int iu, double* W,
                                     mrrr_stream stream);
+
+/*
+ * The dense symmetric eigenproblem A y = lambda y around the tridiagonal
+ * solver: the paper's stages 3-5 (Sec. 1.2; its Fig. of the six stages):
+ * reduction to tridiagonal form A = Q T Q^T by Householder reflectors
+ * (stage 3, mrrr_sytrd), the tridiagonal eigenpairs T z = lambda z
+ * (stage 4, mrrr_stein), and the backtransformation y = Q z (stage 5,
+ * mrrr_ormtr); mrrr_dense_eigh runs the three.  Real symmetric, FP64,
+ * column-major; the reflectors H_j = I - tau_j v_j v_j^T (v_j(j+1) = 1,
+ * v_j(0:j) = 0) are kept below the subdiagonal of A, Q = H_0 ... H_{n-3}.
+ * The reduction is blocked (panels of 32 columns; the trailing update and
+ * the backtransformation run on the FP64 tensor cores); every reduction
+ * sums in a fixed order, so results are deterministic.  Device-side errors
+ * (a non-finite reflector) are read with mrrr_dense_status; those of the
+ * tridiagonal solve with mrrr_get_status.
+ */
+
+/* Bytes of workspace for mrrr_sytrd, mrrr_ormtr (k columns) and
+   mrrr_dense_eigh (k = iu - il + 1 eigenpairs) of order n. */
+mrrr_status mrrr_dense_workspace_size(const mrrr_plan* plan, int n, int k, size_t* bytes);
+
+/* Stage 3: T = Q^T A Q.  A: device, n x n, lda >= n, symmetric, its lower
+   triangle read; on return the diagonal and subdiagonal of A are T's and
+   the reflectors lie below the subdiagonal (the upper triangle is not
+   referenced).  d[n], e[n-1], tau[n-2]: device outputs.  Asynchronous on
+   stream. */
+mrrr_status mrrr_sytrd(mrrr_plan* plan, int n, double* A, int64_t lda, double* d, double* e, double* tau,
+                       void* workspace, size_t ws_bytes, mrrr_stream stream);
+
+/* Stage 5: Y <- Q Y for Y (device, n x k, ldy >= n) with A and tau as
+   mrrr_sytrd leaves them.  Asynchronous. */
+mrrr_status mrrr_ormtr(mrrr_plan* plan, int n, int k, const double* A, int64_t lda, const double* tau, double* Y,
+                       int64_t ldy, void* workspace, size_t ws_bytes, mrrr_stream stream);
+
+/* Stages 3-5: eigenvalues il..iu (1-based, inclusive) of the symmetric A,
+   ascending, into W[iu-il+1], and their eigenvectors into Y (n x (iu-il+1),
+   ldy >= n; NULL for eigenvalues only).  A is overwritten as by
+   mrrr_sytrd.  Synchronisation of the tridiagonal stage as in mrrr_stein. */
+mrrr_status mrrr_dense_eigh(mrrr_plan* plan, int n, double* A, int64_t lda, int il, int iu, double* W, double* Y,
+                            int64_t ldy, void* workspace, size_t ws_bytes, mrrr_stream stream);
+
+/*
+ * The generalized symmetric-definite eigenproblem A x = lambda B x (B
+ * positive definite), the paper's six stages (Sec. 1.2): B = L L^T
+ * (stage 1, mrrr_potrf), C = L^-1 A L^-T (stage 2, mrrr_sygst), the
+ * eigenpairs of C (stages 3-5, mrrr_dense_eigh), X = L^-T Y (stage 6,
+ * mrrr_trsm_lt); mrrr_gen_eigh runs them all.  Blocked by 64; diagonal
+ * blocks are factored and inverted by one CTA each, the rest is FP64
+ * tensor-core GEMM.  Real, FP64, column-major.
+ */
+
+/* Bytes of workspace for the calls below of order n with k eigenvectors. */
+mrrr_status mrrr_gen_workspace_size(const mrrr_plan* plan, int n, int k, size_t* bytes);
+
+/* Stage 1: B (device, n x n, ldb >= n; lower triangle read) <- its Cholesky
+   factor L in the lower triangle (the upper triangle is left as it was).  A
+   pivot that is not positive sets MRRR_ERR_NOTSPD in the device status word
+   (mrrr_dense_status on this workspace).  Asynchronous. */
+mrrr_status mrrr_potrf(mrrr_plan* plan, int n, double* B, int64_t ldb, void* workspace, size_t ws_bytes,
+                       mrrr_stream stream);
+
+/* Stage 2: A (device, n x n, both triangles of the symmetric A) <-
+   L^-1 A L^-T, both triangles, with L the lower triangle of L (ldl >= n).
+   Asynchronous. */
+mrrr_status mrrr_sygst(mrrr_plan* plan, int n, double* A, int64_t lda, const double* L, int64_t ldl,
+                       void* workspace, size_t ws_bytes, mrrr_stream stream);
+
+/* Stage 6: X (device, n x k, ldx >= n) <- L^-T X.  Asynchronous. */
+mrrr_status mrrr_trsm_lt(mrrr_plan* plan, int n, int k, const double* L, int64_t ldl, double* X, int64_t ldx,
+                         void* workspace, size_t ws_bytes, mrrr_stream stream);
+
+/* All six stages: eigenvalues il..iu of the pencil (A, B), ascending, into
+   W[iu-il+1], and their B-orthonormal eigenvectors (X^T B X = I) into X
+   (n x (iu-il+1), ldx >= n; NULL for eigenvalues only).  A (both
+   triangles) and B (lower triangle) are overwritten.  Device-side errors
+   of the dense stages: mrrr_gen_status; of the tridiagonal stage:
+   mrrr_get_status. */
+mrrr_status mrrr_gen_eigh(mrrr_plan* plan, int n, double* A, int64_t lda, double* B, int64_t ldb, int il, int iu,
+                          double* W, double* X, int64_t ldx, void* workspace, size_t ws_bytes, mrrr_stream stream);
+
+/* Synchronise stream and return the first device-side error of the last
+   mrrr_gen_eigh (order n, k eigenpairs) on this workspace: MRRR_ERR_NOTSPD
+   from the Cholesky factorization, MRRR_ERR_NONFINITE from the reduction. */
+mrrr_status mrrr_gen_status(const mrrr_plan* plan, int n, int k, const void* workspace, mrrr_stream stream);
+
+/* Synchronise stream and return the device status word of the last dense
+   call on this workspace (MRRR_ERR_NONFINITE for a non-finite reflector,
+   MRRR_ERR_NOTSPD from the Cholesky factorization). */
+mrrr_status mrrr_dense_status(const void* workspace, mrrr_stream stream);
 
 /* Stage profile of the last solve on a plan.  launches counts the kernels
    the solve ran.  Direct launches: when timing is enabled (mrrr_set_timing)

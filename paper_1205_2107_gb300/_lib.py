@@ -16,16 +16,18 @@ c_double, c_int, c_int64, c_size_t, c_void_p = (ctypes.c_double, ctypes.c_int, c
 
 STATUS = {0: "MRRR_OK", 1: "MRRR_ERR_ARG", 2: "MRRR_ERR_WORKSPACE", 3: "MRRR_ERR_NONFINITE",
           4: "MRRR_ERR_NOCONV", 5: "MRRR_ERR_QUEUE", 6: "MRRR_ERR_TIMEOUT", 7: "MRRR_ERR_CUDA",
-          8: "MRRR_ERR_NOTIMPL", 9: "MRRR_ERR_MARGIN"}
+          8: "MRRR_ERR_NOTIMPL", 9: "MRRR_ERR_MARGIN", 10: "MRRR_ERR_NOTSPD"}
 (OK, ERR_ARG, ERR_WORKSPACE, ERR_NONFINITE, ERR_NOCONV, ERR_QUEUE, ERR_TIMEOUT, ERR_CUDA, ERR_NOTIMPL,
- ERR_MARGIN) = range(10)
+ ERR_MARGIN, ERR_NOTSPD) = range(11)
 
 # every function include/mrrr.h declares
 EXPORTS = ["mrrr_options_default", "mrrr_plan_create", "mrrr_plan_destroy", "mrrr_workspace_size",
            "mrrr_stein", "mrrr_stein_batched", "mrrr_backward", "mrrr_backward_workspace_size",
            "mrrr_get_status", "mrrr_status_string", "mrrr_version", "mrrr_set_timing", "mrrr_get_profile",
            "mrrr_eigenvalues_static", "mrrr_autotune_batched", "mrrr_probe_peak", "mrrr_slice_range",
-           "mrrr_stein_slice"]
+           "mrrr_stein_slice", "mrrr_dense_workspace_size", "mrrr_sytrd", "mrrr_ormtr", "mrrr_dense_eigh",
+           "mrrr_dense_status", "mrrr_gen_workspace_size", "mrrr_potrf", "mrrr_sygst", "mrrr_trsm_lt",
+           "mrrr_gen_eigh", "mrrr_gen_status"]
 STATIC_MAX_N = 8192  # MRRR_STATIC_MAX_N
 
 
@@ -114,6 +116,18 @@ def load(build_if_missing: bool = False):
         lib.mrrr_slice_range.argtypes = [c_int, c_int, c_int, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]
         lib.mrrr_stein_slice.argtypes = [P, c_int, dp, dp, c_int, c_int, c_int, c_int, c_int, dp, dp, c_int64, dp,
                                          c_size_t, P]
+        lib.mrrr_dense_workspace_size.argtypes = [P, c_int, c_int, ctypes.POINTER(c_size_t)]
+        lib.mrrr_sytrd.argtypes = [P, c_int, dp, c_int64, dp, dp, dp, dp, c_size_t, P]
+        lib.mrrr_ormtr.argtypes = [P, c_int, c_int, dp, c_int64, dp, dp, c_int64, dp, c_size_t, P]
+        lib.mrrr_dense_eigh.argtypes = [P, c_int, dp, c_int64, c_int, c_int, dp, dp, c_int64, dp, c_size_t, P]
+        lib.mrrr_dense_status.argtypes = [dp, P]
+        lib.mrrr_gen_workspace_size.argtypes = [P, c_int, c_int, ctypes.POINTER(c_size_t)]
+        lib.mrrr_potrf.argtypes = [P, c_int, dp, c_int64, dp, c_size_t, P]
+        lib.mrrr_sygst.argtypes = [P, c_int, dp, c_int64, dp, c_int64, dp, c_size_t, P]
+        lib.mrrr_trsm_lt.argtypes = [P, c_int, c_int, dp, c_int64, dp, c_int64, dp, c_size_t, P]
+        lib.mrrr_gen_eigh.argtypes = [P, c_int, dp, c_int64, dp, c_int64, c_int, c_int, dp, dp, c_int64, dp,
+                                      c_size_t, P]
+        lib.mrrr_gen_status.argtypes = [P, c_int, c_int, dp, P]
         for name in EXPORTS:
             if name not in ("mrrr_status_string", "mrrr_version"):
                 getattr(lib, name).restype = c_int

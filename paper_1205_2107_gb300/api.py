@@ -419,3 +419,162 @@ def probe_peak(kind: str) -> float:
     rate = ctypes.c_double(0.0)
     _lib.check(_lib.load().mrrr_probe_peak(PEAK_KINDS[kind], ctypes.byref(rate)), "mrrr_probe_peak")
     return float(rate.value)
+
+
+# ---------------------------------------------------------------------------
+# Dense symmetric eigenproblem (the paper's stages 3-5 around the tridiagonal
+# solver).  A symmetric matrix is its own transpose, so a contiguous (n, n)
+# tensor is passed as the column-major matrix itself.
+
+def _dense_ws(plan: Plan, n: int, k: int) -> tuple[torch.Tensor, int]:
+    nbytes = ctypes.c_size_t(0)
+    _lib.check(_lib.load().mrrr_dense_workspace_size(plan.handle, n, k, ctypes.byref(nbytes)),
+               "mrrr_dense_workspace_size")
+    return plan.workspace(nbytes.value), int(nbytes.value)
+
+
+def _dense_check(plan: Plan, ws: torch.Tensor, where: str, device) -> None:
+    rc = _lib.load().mrrr_dense_status(_ptr(ws), _stream_handle(device))
+    if rc != _lib.OK:
+        raise _lib.MrrrError(rc, where)
+
+
+def tridiagonalize(A: torch.Tensor, *, plan: Plan | None = None, check: bool = True):
+    """Stage 3 (mrrr_sytrd): (d, e, tau, R) with T = tridiag(e, d, e) =
+    Q^T A Q; R is A overwritten by the reflectors (below its subdiagonal),
+    which apply_q reads."""
+    A = _check_input(A, "A")
+    n = A.shape[0]
+    if A.dim() != 2 or A.shape[1] != n:
+        raise ValueError("A must be square")
+    R = A.clone()
+    plan = plan or default_plan(A.device)
+    d = torch.empty(max(n, 1), dtype=_F64, device=A.device)
+    e = torch.empty(max(n - 1, 1), dtype=_F64, device=A.device)
+    tau = torch.empty(max(n - 2, 1), dtype=_F64, device=A.device)
+    ws, nbytes = _dense_ws(plan, n, 0)
+    _lib.check(_lib.load().mrrr_sytrd(plan.handle, n, _ptr(R), n, _ptr(d), _ptr(e), _ptr(tau), _ptr(ws), nbytes,
+                                      _stream_handle(A.device)), "mrrr_sytrd")
+    if check:
+        _dense_check(plan, ws, "mrrr_sytrd", A.device)
+    return d[:n], e[:max(n - 1, 0)], tau[:max(n - 2, 0)], R
+
+
+def apply_q(R: torch.Tensor, tau: torch.Tensor, Y: torch.Tensor, *, plan: Plan | None = None) -> torch.Tensor:
+    """Stage 5 (mrrr_ormtr): Q Y for the Q of tridiagonalize; Y is (n, k)
+    and is returned as a new column-major (n, k) view."""
+    R = _check_input(R, "R")
+    n = R.shape[0]
+    k = Y.shape[1]
+    plan = plan or default_plan(R.device)
+    Yt = _check_input(Y, "Y").t().contiguous()  # (k, n) row-major = column-major Y
+    ws, nbytes = _dense_ws(plan, n, min(k, n))
+    _lib.check(_lib.load().mrrr_ormtr(plan.handle, n, k, _ptr(R), n, _ptr(tau), _ptr(Yt), n, _ptr(ws), nbytes,
+                                      _stream_handle(R.device)), "mrrr_ormtr")
+    return Yt.t()
+
+
+def eigh_dense(A: torch.Tensor, il: int | None = None, iu: int | None = None, *, vectors: bool = True,
+               plan: Plan | None = None, check: bool = True):
+    """Eigenpairs il..iu (1-based, inclusive; default all) of the symmetric A
+    (mrrr_dense_eigh: reduction, tridiagonal MRRR, backtransformation).
+    Returns (W, Y) with Y (n, k) column-major, or W alone."""
+    A = _check_input(A, "A")
+    n = A.shape[0]
+    if A.dim() != 2 or A.shape[1] != n:
+        raise ValueError("A must be square")
+    il = 1 if il is None else int(il)
+    iu = n if iu is None else int(iu)
+    if n == 0:
+        W = torch.empty(0, dtype=_F64, device=A.device)
+        return (W, torch.empty((0, 0), dtype=_F64, device=A.device)) if vectors else W
+    if not 1 <= il <= iu <= n:
+        raise ValueError("need 1 <= il <= iu <= n")
+    k = iu - il + 1
+    plan = plan or default_plan(A.device)
+    R = A.clone()
+    W = torch.empty(k, dtype=_F64, device=A.device)
+    Yt = torch.empty((k, n), dtype=_F64, device=A.device) if vectors else None
+    for attempt in range(4):
+        ws, nbytes = _dense_ws(plan, n, k)
+        R.copy_(A)
+        _lib.check(_lib.load().mrrr_dense_eigh(plan.handle, n, _ptr(R), n, il, iu, _ptr(W), _ptr(Yt), n, _ptr(ws),
+                                               nbytes, _stream_handle(A.device)), "mrrr_dense_eigh")
+        if not check:
+            break
+        _dense_check(plan, ws, "mrrr_dense_eigh", A.device)
+        info = plan.info()
+        if info["status"] == _lib.ERR_QUEUE and attempt < 3:
+            plan.set_options(pool_rows=max(int(info["pool_rows_used"] * 2) + 1024, plan.options.get("pool_rows", 0)),
+                             max_nodes=max(int(max(info["nodes"], 16) * 2), plan.options.get("max_nodes", 0)))
+            continue
+        if info["status"] != _lib.OK:
+            raise _lib.MrrrError(info["status"], "mrrr_dense_eigh")
+        break
+    return (W, Yt.t()) if vectors else W
+
+
+# ---------------------------------------------------------------------------
+# Generalized symmetric-definite eigenproblem A x = lambda B x (the paper's
+# six stages).
+
+def _gen_ws(plan: Plan, n: int, k: int) -> tuple[torch.Tensor, int]:
+    nbytes = ctypes.c_size_t(0)
+    _lib.check(_lib.load().mrrr_gen_workspace_size(plan.handle, n, k, ctypes.byref(nbytes)),
+               "mrrr_gen_workspace_size")
+    return plan.workspace(nbytes.value), int(nbytes.value)
+
+
+def cholesky(B: torch.Tensor, *, plan: Plan | None = None) -> torch.Tensor:
+    """Stage 1 (mrrr_potrf): the lower-triangular L with L L^T = B."""
+    B = _check_input(B, "B")
+    n = B.shape[0]
+    plan = plan or default_plan(B.device)
+    Lt = B.clone()  # column-major storage of B (symmetric)
+    ws, nbytes = _gen_ws(plan, n, 0)
+    _lib.check(_lib.load().mrrr_potrf(plan.handle, n, _ptr(Lt), n, _ptr(ws), nbytes, _stream_handle(B.device)),
+               "mrrr_potrf")
+    rc = _lib.load().mrrr_dense_status(_ptr(ws), _stream_handle(B.device))
+    if rc != _lib.OK:
+        raise _lib.MrrrError(rc, "mrrr_potrf")
+    return torch.tril(Lt.t())  # the column-major lower factor, as a row-major (n, n) tensor
+
+
+def eigh_generalized(A: torch.Tensor, B: torch.Tensor, il: int | None = None, iu: int | None = None, *,
+                     vectors: bool = True, plan: Plan | None = None, check: bool = True):
+    """Eigenpairs il..iu of A x = lambda B x (A symmetric, B symmetric
+    positive definite; mrrr_gen_eigh): (W, X) with X^T B X = I, X (n, k)
+    column-major, or W alone."""
+    A = _check_input(A, "A")
+    B = _check_input(B, "B")
+    n = A.shape[0]
+    il = 1 if il is None else int(il)
+    iu = n if iu is None else int(iu)
+    if n == 0:
+        W = torch.empty(0, dtype=_F64, device=A.device)
+        return (W, torch.empty((0, 0), dtype=_F64, device=A.device)) if vectors else W
+    if not 1 <= il <= iu <= n:
+        raise ValueError("need 1 <= il <= iu <= n")
+    k = iu - il + 1
+    plan = plan or default_plan(A.device)
+    W = torch.empty(k, dtype=_F64, device=A.device)
+    Xt = torch.empty((k, n), dtype=_F64, device=A.device) if vectors else None
+    for attempt in range(4):
+        Ac, Bc = A.clone(), B.clone()
+        ws, nbytes = _gen_ws(plan, n, k)
+        _lib.check(_lib.load().mrrr_gen_eigh(plan.handle, n, _ptr(Ac), n, _ptr(Bc), n, il, iu, _ptr(W), _ptr(Xt), n,
+                                             _ptr(ws), nbytes, _stream_handle(A.device)), "mrrr_gen_eigh")
+        if not check:
+            break
+        rc = _lib.load().mrrr_gen_status(plan.handle, n, k, _ptr(ws), _stream_handle(A.device))
+        if rc != _lib.OK:
+            raise _lib.MrrrError(rc, "mrrr_gen_eigh")
+        info = plan.info()
+        if info["status"] == _lib.ERR_QUEUE and attempt < 3:
+            plan.set_options(pool_rows=max(int(info["pool_rows_used"] * 2) + 1024, plan.options.get("pool_rows", 0)),
+                             max_nodes=max(int(max(info["nodes"], 16) * 2), plan.options.get("max_nodes", 0)))
+            continue
+        if info["status"] != _lib.OK:
+            raise _lib.MrrrError(info["status"], "mrrr_gen_eigh")
+        break
+    return (W, Xt.t()) if vectors else W

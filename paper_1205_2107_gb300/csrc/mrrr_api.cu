@@ -166,16 +166,18 @@ struct Layout {
 };
 
 // Threads of the eigenvector kernel (persistent; one vector at a time per
-// thread): vec_blocks_per_sm CTAs of 128 per SM, no more than there are
-// eigenpairs, and -- each thread owning 2 n_max doubles of interleaved
-// scratch -- no more than fit in 16 GB of scratch, but never fewer than one
-// warp per SM sub-partition.
+// thread): c CTAs of 128 on every SM -- the same number on each, so that
+// every SM sub-partition holds c warps and the scheduler's ranks spread the
+// 32-vector chunks evenly -- with c the number of chunk waves over the
+// 4 nsm sub-partitions, at most vec_blocks_per_sm, and at most what fits in
+// 32 GB of scratch (each thread owns 2 n_max doubles), but at least one.
 int64_t vec_threads(const mrrr_plan* p, int64_t max_slots, int n_max) {
-  const int64_t cap = (int64_t)p->nsm * std::max(1, p->opt.vec_blocks_per_sm) * 128;
-  const int64_t floor_t = (int64_t)p->nsm * 128;
-  const int64_t mem_t = ((int64_t)16 << 30) / (16 * (int64_t)std::max(n_max, 1)) / 128 * 128;
-  const int64_t t = std::min(cap, std::max(floor_t, mem_t));
-  return std::max<int64_t>(128, std::min(t, (max_slots + 127) / 128 * 128));
+  const int64_t per_wave = (int64_t)p->nsm * 128;  // one warp per sub-partition
+  const int64_t waves = (max_slots + per_wave - 1) / per_wave;
+  const int64_t mem_c = ((int64_t)32 << 30) / (16 * (int64_t)std::max(n_max, 1)) / per_wave;
+  const int64_t c = std::max<int64_t>(1, std::min<int64_t>({waves, (int64_t)std::max(1, p->opt.vec_blocks_per_sm),
+                                                           mem_c}));
+  return per_wave * c;
 }
 
 Layout make_layout(const mrrr_plan* p, int batch, int64_t n_total, int64_t k_total, int n_max) {
@@ -824,6 +826,7 @@ const char* mrrr_status_string(mrrr_status s) {
     case MRRR_ERR_CUDA: return "CUDA runtime error";
     case MRRR_ERR_NOTIMPL: return "not implemented";
     case MRRR_ERR_MARGIN: return "slice margin too small for a cluster at the slice boundary";
+    case MRRR_ERR_NOTSPD: return "matrix not positive definite";
   }
   return "unknown status";
 }
