@@ -459,9 +459,15 @@ def run_ours(args, rank: int, world: int):
                "sample": sample_text(windows, len(mats), cores, t), "host": host_cpu()}
     side = None
     large = None
+    dense = None
+    mixed = None
+    shard = None
     if not args.no_side:
         side = side_by_side(args, dev, flush)
         large = large_legs(dev, flush)
+        dense = dense_legs(dev, flush)
+        mixed = mixed_precision_leg(dev, flush)
+        shard = shard_leg(dev, flush)
     clocks = clk.summary()
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -482,7 +488,7 @@ def run_ours(args, rank: int, world: int):
                       "fp64_div_g_per_s": PEAKS["ddiv"] / 1e9 if PEAKS["ddiv"] else None,
                       "source": PEAKS["source"]},
             "batched": side["batched"] if side else None, "adjoint": side["adjoint"] if side else None,
-            "large_n50000": large,
+            "large_n50000": large, "dense": dense, "mixed_precision": mixed, "index_slices": shard,
             "stages_ms_per_step": {k: v / args.steps for k, v in sorted(stage_ms.items())},
             "stages_source": "timed graph replays: GPU global timer read by one-thread kernels at the stage "
                              "boundaries inside the graph, summed over the steps",
@@ -577,6 +583,162 @@ def large_legs(dev, flush):
                      "path_roofline_frac": 1e3 * t_roof / ms, "timing": "CUDA graph replay, CUDA events"}
         del plan
         torch.cuda.empty_cache()
+    return out
+
+
+def _sampled_accuracy(A, W, Y, seed=0, ncols=256):
+    """Residual max ||A y - lambda y|| / (n eps ||A||) and orthogonality
+    max |Y^T Y_s - I_s| / (n eps) over a seeded sample of columns (the
+    dense problem's accuracy goals, checked at any size)."""
+    import torch
+    eps = 2.0 ** -53
+    n = A.shape[0]
+    k = W.numel()
+    cols = torch.as_tensor(np.sort(np.random.default_rng(seed).choice(k, min(k, ncols), replace=False)),
+                           device=A.device)
+    Ys = Y[:, cols]
+    nrm = float(W.abs().max())
+    res = float(torch.linalg.vector_norm(A @ Ys - Ys * W[cols][None, :], dim=0).max())
+    G = Y.t() @ Ys
+    G[cols, torch.arange(cols.numel(), device=A.device)] -= 1.0
+    return {"residual": res / (n * eps * nrm), "orthogonality": float(G.abs().max()) / (n * eps)}
+
+
+def dense_legs(dev, flush):
+    """The dense stages around the tridiagonal solver (paper Sec. 1.2) on
+    one GPU, n = 8000: the standard problem A y = lambda y (stage 3
+    reduction, stage 4 MRRR, stage 5 backtransformation) and the generalized
+    A x = lambda B x (adding stage 1 Cholesky, stage 2 reduction, stage 6
+    backtransformation); A symmetric with N(0,1) entries (seed 8000),
+    B = G G^T + n I.  Each stage timed with CUDA events (mean of two after a
+    warm-up), against its bound: the reduction's symmetric products on the
+    FP64 FMA pipe and its rank-2k updates on the FP64 MMA, every other
+    stage a GEMM-shaped contraction on the FP64 MMA."""
+    import torch
+    from paper_1205_2107_gb300 import api
+    n = 8000
+    rng = np.random.default_rng(8000)
+    X = rng.standard_normal((n, n))
+    A = torch.tensor((X + X.T) / 2, device=dev)
+    G = rng.standard_normal((n, n))
+    B = torch.tensor(G @ G.T + n * np.eye(n), device=dev)
+    del X, G
+    plan = api.Plan(dev)
+    fma_peak, mma_peak = PEAKS["dfma"], PEAKS["dmma"] or PEAKS["dfma"]
+    W, Y = api.eigh_dense(A, plan=plan)
+    acc = _sampled_accuracy(A, W, Y)
+    d, e, tau, R = api.tridiagonalize(A, plan=plan)
+    eo = torch.cat([e, e.new_zeros(1)])
+    t_trd = _time_cuda(lambda: api.tridiagonalize(A, plan=plan, check=False), 2, flush)
+    t_step = _time_cuda(lambda: api.eigh_tridiagonal(d, eo, plan=plan, check=False), 2, flush)
+    Z = api.eigh_tridiagonal(d, eo, plan=plan)[1]
+    t_orm = _time_cuda(lambda: api.apply_q(R, tau, Z, plan=plan), 2, flush)
+    t_all = _time_cuda(lambda: api.eigh_dense(A, plan=plan, check=False), 2, flush)
+    f_half = 2.0 / 3.0 * n ** 3
+    trd_roof = 1e3 * (f_half / fma_peak + f_half / mma_peak)
+    standard = {
+        "workload": "dense symmetric n=8000, N(0,1) entries (seed 8000), all eigenpairs",
+        "ms": t_all, "eigenpairs_per_s": n / (t_all * 1e-3),
+        "stages_ms": {"reduction": t_trd, "tridiagonal_mrrr": t_step, "backtransformation": t_orm},
+        "roofline": {"reduction_frac": trd_roof / t_trd,
+                     "backtransformation_tflops": 2.0 * n ** 3 / (t_orm * 1e-3) / 1e12,
+                     "backtransformation_frac": 2.0 * n ** 3 / (t_orm * 1e-3) / mma_peak,
+                     "model": "reduction 4/3 n^3 flops (half on the FP64 FMA pipe, half on the FP64 MMA), "
+                              "backtransformation 2 n^2 k on the FP64 MMA"},
+        "accuracy_sampled": acc}
+    del R, Z, Y
+    Wg, Xg = api.eigh_generalized(A, B, plan=plan)
+    Bx = B @ Xg[:, :256]
+    gacc = {"b_orthogonality": float((Xg.t() @ Bx - torch.eye(n, 256, dtype=torch.float64, device=dev)).abs().max())
+            / (n * 2.0 ** -53)}
+    del Bx, Xg
+    t_chol = _time_cuda(lambda: api.cholesky(B, plan=plan), 2, flush)
+    t_gen = _time_cuda(lambda: api.eigh_generalized(A, B, plan=plan, check=False), 2, flush)
+    generalized = {
+        "workload": "generalized A x = lambda B x, n=8000, A as above, B = G G^T + n I (G N(0,1)), all eigenpairs",
+        "ms": t_gen, "eigenpairs_per_s": n / (t_gen * 1e-3),
+        "stages_ms": {"cholesky": t_chol, "standard_problem": t_all,
+                      "reduction_and_backtransformation": t_gen - t_chol - t_all},
+        "roofline": {"cholesky_tflops": n ** 3 / 3.0 / (t_chol * 1e-3) / 1e12,
+                     "cholesky_frac": n ** 3 / 3.0 / (t_chol * 1e-3) / mma_peak,
+                     "stage2_and_6_frac": 3.0 * n ** 3 / ((t_gen - t_chol - t_all) * 1e-3) / mma_peak,
+                     "model": "Cholesky n^3/3, L^-1 A L^-T 2 n^3 (two triangular solves), L^-T Y n^3"},
+        "accuracy_sampled": gacc}
+    del A, B
+    torch.cuda.empty_cache()
+    return {"standard_n8000": standard, "generalized_n8000": generalized}
+
+
+def shard_leg(dev, flush, nslices=4):
+    """Index-range sharding (paper Sec. 3.1.2) of the clustered n ~ 20,000
+    matrices of the headline step: for each, the slices of nslices equal
+    parts solved one after the other on this GPU, as nslices GPUs would
+    solve them side by side; the time such a job would take is the slowest
+    slice (no data moves between slices), against one GPU solving the whole
+    matrix.  Clusters that cross a slice boundary are computed whole by both
+    neighbouring slices (W+'s pairs, glued W21+'s groups of up to 1,904
+    equal eigenvalues, which grow the margin).  Columns of neighbouring
+    slices are checked for orthogonality across each boundary."""
+    import torch
+    from paper_1205_2107_gb300 import api
+    out = {}
+    for name, d, e in workload_matrices():
+        n = len(d)
+        dt = torch.tensor(d, device=dev)
+        et = torch.tensor(np.append(e, 0.0), device=dev)
+        plan = api.Plan(dev)
+        api.eigh_tridiagonal(dt, et, plan=plan)
+        t_full = _time_cuda(lambda: api.eigh_tridiagonal(dt, et, plan=plan, check=False), 1, flush)
+        times, edges, margins = [], [], []
+        prev = None
+        for sl in range(nslices):
+            splan = api.Plan(dev)
+            W, Z, (a, b) = api.eigh_tridiagonal_slice(dt, et, 1, n, nslices, sl, plan=splan)
+            # the margin the checked call settled on: grow until the status is clean
+            m = 32
+            while True:
+                api.eigh_tridiagonal_slice(dt, et, 1, n, nslices, sl, margin=m, plan=splan, check=False)
+                if splan.info()["status"] == 0 or m > n:
+                    break
+                m *= 4
+            margins.append(m)
+            times.append(_time_cuda(lambda: api.eigh_tridiagonal_slice(dt, et, 1, n, nslices, sl, margin=m,
+                                                                      plan=splan, check=False), 1, flush))
+            if prev is not None:  # last 512 columns of the previous slice against the first 512 of this one
+                G = prev.t() @ Z[:, :512]
+                edges.append(float(G.abs().max()) / (n * 2.0 ** -53))
+            prev = Z[:, -512:].clone()
+            del W, Z, splan
+            torch.cuda.empty_cache()
+        out[name] = {"n": n, "slices": nslices, "full_ms": t_full, "slice_ms": times, "job_ms": max(times),
+                     "speedup_over_one_gpu": t_full / max(times), "efficiency": t_full / max(times) / nslices,
+                     "margins": margins, "boundary_orthogonality_n_eps": edges}
+    out["note"] = "slices timed one after the other on one GPU; a job on as many GPUs takes the slowest slice"
+    return out
+
+
+def mixed_precision_leg(dev, flush):
+    """Eigenvectors in double-double (vector_precision = 2) against FP64 on
+    the same tridiagonal: uniform random n=20000 (seed 1205), all
+    eigenpairs; time and orthogonality (sampled: all columns against 1,024
+    seeded ones and a +-256 band)."""
+    import torch
+    from paper_1205_2107_gb300 import api
+    d, e = inputs.uniform(20000, 1205)
+    dt = torch.tensor(d, device=dev)
+    et = torch.tensor(np.append(e, 0.0), device=dev)
+    n = len(d)
+    out = {}
+    for name, prec in (("fp64", 1), ("double_double", 2)):
+        plan = api.Plan(dev, vector_precision=prec)
+        W, Z = api.eigh_tridiagonal(dt, et, plan=plan)
+        ms = _time_cuda(lambda: api.eigh_tridiagonal(dt, et, plan=plan, check=False), 2, flush)
+        acc = verify_solution(dt, et, W, Z)
+        out[name] = {"ms": ms, "eigenpairs_per_s": n / (ms * 1e-3),
+                     "orthogonality_n_eps": acc["orthogonality"] * 20, "residual_n_eps": acc["residual"] * 20}
+        del W, Z, plan
+        torch.cuda.empty_cache()
+    out["workload"] = "uniform random tridiagonal n=20000 (seed 1205), all eigenpairs"
     return out
 
 

@@ -103,7 +103,16 @@ typedef struct mrrr_options {
                               Gershgorin end nearer the wanted indices (default), 1 the left
                               end, 2 the right end (slices of one index range that must share
                               one root representation) */
-  int reserved_[6];        /* zero */
+  int vector_precision;    /* arithmetic of the eigenvector stage: 1 FP64 (default); 2
+                              double-double (about 106 bits) -- each singleton's eigenvalue
+                              is corrected once by the Rayleigh quotient of a double-double
+                              twisted factorization on its representation, then its vector
+                              is solved at the corrected value, also in double-double, and
+                              rounded to FP64: vectors taken from one representation are
+                              then eigenvectors of one matrix to about eps^2 / relgap, so
+                              orthogonality improves (Sec. 2.3, higher internal precision);
+                              several times the FP64 stage's time */
+  int reserved_[5];        /* zero */
 } mrrr_options;
 
 /* Counters reported by mrrr_get_status (device values after the last solve). */

@@ -170,11 +170,13 @@ struct Layout {
 // every SM sub-partition holds c warps and the scheduler's ranks spread the
 // 32-vector chunks evenly -- with c the number of chunk waves over the
 // 4 nsm sub-partitions, at most vec_blocks_per_sm, and at most what fits in
-// 32 GB of scratch (each thread owns 2 n_max doubles), but at least one.
+// 32 GB of scratch (each thread owns 2 n_max doubles, 4 in double-double),
+// but at least one.
 int64_t vec_threads(const mrrr_plan* p, int64_t max_slots, int n_max) {
   const int64_t per_wave = (int64_t)p->nsm * 128;  // one warp per sub-partition
   const int64_t waves = (max_slots + per_wave - 1) / per_wave;
-  const int64_t mem_c = ((int64_t)32 << 30) / (16 * (int64_t)std::max(n_max, 1)) / per_wave;
+  const int64_t row_bytes = p->opt.vector_precision == 2 ? 32 : 16;  // scratch per row and thread
+  const int64_t mem_c = ((int64_t)32 << 30) / (row_bytes * (int64_t)std::max(n_max, 1)) / per_wave;
   const int64_t c = std::max<int64_t>(1, std::min<int64_t>({waves, (int64_t)std::max(1, p->opt.vec_blocks_per_sm),
                                                            mem_c}));
   return per_wave * c;
@@ -228,8 +230,9 @@ Layout make_layout(const mrrr_plan* p, int batch, int64_t n_total, int64_t k_tot
   // the vector scratch: two interleaved arrays (L+, and s then U-) of
   // vscr_rows rows per thread; it also holds the FP32 copy of the root rows
   // (one float2 per row) during root bisection
+  const size_t arrays = o.vector_precision == 2 ? 4 : 2;  // double-double: hi and lo of each
   L.vscr = take(sizeof(double) *
-                std::max<size_t>(2 * (size_t)L.vscr_threads * (size_t)L.vscr_rows, (size_t)n_total));
+                std::max<size_t>(arrays * (size_t)L.vscr_threads * (size_t)L.vscr_rows, (size_t)n_total));
   L.total = off;
   return L;
 }
@@ -286,6 +289,7 @@ Dev make_dev(const mrrr_plan* p, const Layout& L, void* ws, int batch, const dou
   v.width_scale = o.width_scale;
   v.fixed_width = o.multisection_width;
   v.root_side = o.root_side;
+  v.vec_dd = o.vector_precision == 2;
   return v;
 }
 
@@ -542,6 +546,7 @@ mrrr_status mrrr_options_default(mrrr_options* opt) {
   opt->root_perturb = 64.0;
   opt->engine_blocks_per_sm = 2;
   opt->width_scale = 1.0;
+  opt->vector_precision = 1;
   return MRRR_OK;
 }
 
@@ -567,9 +572,12 @@ mrrr_status mrrr_plan_create(mrrr_plan** plan, const mrrr_options* opt) {
     if (opt->width_scale > 0) o.width_scale = opt->width_scale;
     if (opt->multisection_width > 0) o.multisection_width = opt->multisection_width;
     if (opt->root_side > 0) o.root_side = opt->root_side;
+    if (opt->vector_precision > 0) o.vector_precision = opt->vector_precision;
   }
   const int mw = o.multisection_width;
-  if (mw < 0 || mw > 32 || (mw & (mw - 1)) != 0 || o.root_side < 0 || o.root_side > 2) return MRRR_ERR_ARG;
+  if (mw < 0 || mw > 32 || (mw & (mw - 1)) != 0 || o.root_side < 0 || o.root_side > 2 ||
+      o.vector_precision < 0 || o.vector_precision > 2)
+    return MRRR_ERR_ARG;
   if (o.gap_tol >= 1.0 || o.classify_rtol >= 0.25 || o.threads_per_block % 32 != 0) return MRRR_ERR_ARG;
   int dev = 0, nsm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return MRRR_ERR_CUDA;

@@ -43,31 +43,31 @@ __device__ __forceinline__ void dmma(double& c0, double& c1, double a, double b)
 }
 
 // As(rr, kk) = A(m0 + rr, k0 + kk), zero outside; stored K-contiguous.
-__device__ __forceinline__ void load_a(double* As, const GemmArgs& g, int m0, int k0) {
+__device__ __forceinline__ void load_a(double* As, const GemmArgs& g, int m0, int k0, int kend) {
   if (g.a_cs == 1) {  // K contiguous in memory
     for (int idx = threadIdx.x; idx < kTM * kTK; idx += blockDim.x) {
       const int rr = idx / kTK, kk = idx % kTK, i = m0 + rr, p = k0 + kk;
-      As[rr * kKS + kk] = (i < g.m && p < g.k) ? g.A[(int64_t)i * g.a_rs + p] : 0.0;
+      As[rr * kKS + kk] = (i < g.m && p < kend) ? g.A[(int64_t)i * g.a_rs + p] : 0.0;
     }
   } else {  // rows contiguous (or general strides)
     for (int idx = threadIdx.x; idx < kTM * kTK; idx += blockDim.x) {
       const int kk = idx / kTM, rr = idx % kTM, i = m0 + rr, p = k0 + kk;
-      As[rr * kKS + kk] = (i < g.m && p < g.k) ? g.A[(int64_t)i * g.a_rs + (int64_t)p * g.a_cs] : 0.0;
+      As[rr * kKS + kk] = (i < g.m && p < kend) ? g.A[(int64_t)i * g.a_rs + (int64_t)p * g.a_cs] : 0.0;
     }
   }
 }
 
 // Bs(cc, kk) = B(k0 + kk, n0 + cc), zero outside; stored K-contiguous.
-__device__ __forceinline__ void load_b(double* Bs, const GemmArgs& g, int n0, int k0) {
+__device__ __forceinline__ void load_b(double* Bs, const GemmArgs& g, int n0, int k0, int kend) {
   if (g.b_rs == 1) {  // K contiguous in memory
     for (int idx = threadIdx.x; idx < kTN * kTK; idx += blockDim.x) {
       const int cc = idx / kTK, kk = idx % kTK, j = n0 + cc, p = k0 + kk;
-      Bs[cc * kKS + kk] = (j < g.n && p < g.k) ? g.B[p + (int64_t)j * g.b_cs] : 0.0;
+      Bs[cc * kKS + kk] = (j < g.n && p < kend) ? g.B[p + (int64_t)j * g.b_cs] : 0.0;
     }
   } else {
     for (int idx = threadIdx.x; idx < kTN * kTK; idx += blockDim.x) {
       const int kk = idx / kTN, cc = idx % kTN, j = n0 + cc, p = k0 + kk;
-      Bs[cc * kKS + kk] = (j < g.n && p < g.k) ? g.B[(int64_t)p * g.b_rs + (int64_t)j * g.b_cs] : 0.0;
+      Bs[cc * kKS + kk] = (j < g.n && p < kend) ? g.B[(int64_t)p * g.b_rs + (int64_t)j * g.b_cs] : 0.0;
     }
   }
 }
@@ -81,9 +81,16 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm(GemmArgs g) {
   const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
   const int r = lane >> 2, c = lane & 3;
   double acc[4][4][2] = {};
-  for (int k0 = 0; k0 < g.k; k0 += kTK) {
-    load_a(As, g, m0, k0);
-    load_b(Bs, g, n0, k0);
+  int kbeg = 0, kend = g.k;
+  double* C = g.C;
+  if (g.kchunk > 0) {
+    kbeg = blockIdx.z * g.kchunk;
+    kend = min(g.k, kbeg + g.kchunk);
+    C += (int64_t)blockIdx.z * g.cstride;
+  }
+  for (int k0 = kbeg; k0 < kend; k0 += kTK) {
+    load_a(As, g, m0, k0, kend);
+    load_b(Bs, g, n0, k0, kend);
     __syncthreads();
 #pragma unroll
     for (int kq = 0; kq < kTK; kq += 4) {
@@ -108,7 +115,7 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm(GemmArgs g) {
       for (int h = 0; h < 2; ++h) {
         const int row = m0 + wm + 8 * i + r, col = n0 + wn + 8 * j + c2 + h;
         if (row < g.m && col < g.n && (!g.lower || row >= col)) {
-          double* p = g.C + row + (int64_t)col * g.ldc;
+          double* p = C + row + (int64_t)col * g.ldc;
           *p = g.beta == 0.0 ? g.alpha * acc[i][j][h] : fma(g.alpha, acc[i][j][h], g.beta * *p);
         }
       }
@@ -116,9 +123,52 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm(GemmArgs g) {
 
 void gemm(const GemmArgs& g, cudaStream_t s) {
   if (g.m <= 0 || g.n <= 0) return;
+  GemmArgs h = g;
+  h.kchunk = 0;
   dim3 grid((g.m + kTM - 1) / kTM, (g.n + kTN - 1) / kTN);
-  k_gemm<<<grid, kGemmThreads, 0, s>>>(g);
+  k_gemm<<<grid, kGemmThreads, 0, s>>>(h);
   count_launch();
+}
+
+namespace {
+// C(i, j) = alpha sum_z P_z(i, j) + beta C(i, j), z in order.
+__global__ void k_splitk_reduce(const double* P, int nsplit, int64_t pstride, int m, int n, double alpha,
+                                double beta, double* C, int64_t ldc) {
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < (int64_t)m * n;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(idx / m), i = (int)(idx % m);
+    double sacc = 0.0;
+    for (int z = 0; z < nsplit; ++z) sacc += P[z * pstride + i + (int64_t)j * m];
+    double* c = C + i + (int64_t)j * ldc;
+    *c = beta == 0.0 ? alpha * sacc : fma(alpha, sacc, beta * *c);
+  }
+}
+}  // namespace
+
+void gemm_splitk(GemmArgs g, double* partials, int max_split, int nsm, cudaStream_t s) {
+  if (g.m <= 0 || g.n <= 0) return;
+  const int64_t tiles = (int64_t)((g.m + kTM - 1) / kTM) * ((g.n + kTN - 1) / kTN);
+  // enough CTAs for four per SM, K chunks of at least 256
+  int64_t split = std::min<int64_t>({(int64_t)max_split, (4LL * nsm + tiles - 1) / tiles, (g.k + 255) / 256});
+  if (split <= 1 || g.lower) {
+    gemm(g, s);
+    return;
+  }
+  const int kchunk = (int)(((g.k + split - 1) / split + kTK - 1) / kTK * kTK);
+  split = (g.k + kchunk - 1) / kchunk;
+  GemmArgs h = g;
+  h.C = partials;
+  h.ldc = g.m;
+  h.alpha = 1.0;
+  h.beta = 0.0;
+  h.kchunk = kchunk;
+  h.cstride = (int64_t)g.m * g.n;
+  dim3 grid((g.m + kTM - 1) / kTM, (g.n + kTN - 1) / kTN, (unsigned)split);
+  k_gemm<<<grid, kGemmThreads, 0, s>>>(h);
+  const int64_t tot = (int64_t)g.m * g.n;
+  k_splitk_reduce<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(8192, (tot + 255) / 256)), 256, 0, s>>>(
+      partials, (int)split, h.cstride, g.m, g.n, g.alpha, g.beta, g.C, g.ldc);
+  count_launch(2);
 }
 
 // Column-major operands: op(X) = X (ld) or X^T.
@@ -341,6 +391,19 @@ __global__ void __launch_bounds__(kRowCta) k_trd_wfix(TrdArgs t, int j, int i) {
   if (r < t.n) t.W[r + i * n] -= s_c * t.V[r + i * n];
 }
 
+// Columns c0 .. c1-1 of an n-row column-major panel to zero.
+__global__ void k_zero_cols(double* X, int n, int c0, int c1) {
+  const int64_t tot = (int64_t)n * (c1 - c0);
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < tot; idx += (int64_t)gridDim.x * blockDim.x)
+    X[(int64_t)c0 * n + idx] = 0.0;
+}
+
+__global__ void k_copy_block(const double* src, double* dst, int64_t count) {
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < count;
+       idx += (int64_t)gridDim.x * blockDim.x)
+    dst[idx] = src[idx];
+}
+
 // The last diagonal and subdiagonal entries (untouched by any reflector).
 __global__ void k_trd_tail(TrdArgs t) {
   const int n = t.n;
@@ -361,7 +424,7 @@ __global__ void k_trd_tail(TrdArgs t) {
 size_t trd_scratch_doubles(int n) {
   const int64_t T = (std::max(n - 1, 1) + kSymvTile - 1) / kSymvTile;
   const int64_t rc = (std::max(n, 1) + kRowCta - 1) / kRowCta;
-  return (size_t)(2 * (int64_t)n * kNb + T * T * kSymvTile + rc * (2 + 2 * kNb));
+  return (size_t)(3 * (int64_t)n * kNb + T * T * kSymvTile + rc * (2 + 2 * kNb));
 }
 
 TrdArgs trd_args(int n, double* A, int64_t lda, double* d, double* e, double* tau, double* scratch, DenseCtl* ctl) {
@@ -378,7 +441,7 @@ TrdArgs trd_args(int n, double* A, int64_t lda, double* d, double* e, double* ta
   t.V = p;
   p += (int64_t)n * kNb;
   t.W = p;
-  p += (int64_t)n * kNb;
+  p += 2 * (int64_t)n * kNb;  // W, then the copy of V used by the trailing update
   t.P = p;
   p += T * T * kSymvTile;
   t.colpart = p;
@@ -405,11 +468,20 @@ void launch_trd(const TrdArgs& t, cudaStream_t s) {
       k_trd_wfix<<<row_ctas(m), kRowCta, 0, s>>>(t, j, i);
       count_launch(5);
     }
-    // trailing update of the lower triangle: A22 -= V W^T + W V^T
+    // trailing update of the lower triangle, A22 -= V W^T + W V^T, as one
+    // GEMM of depth 2 kNb: V, W and a copy of V lie side by side (n x 3 kNb),
+    // so [V W] and [W V] are both column ranges of it
     const int j1 = j0 + ncols, m2 = n - j1;
     double* C = t.A + j1 + (int64_t)j1 * t.lda;
-    gemm(gemm_args(m2, m2, ncols, -1.0, t.V + j1, n, false, t.W + j1, n, true, 1.0, C, t.lda, true), s);
-    gemm(gemm_args(m2, m2, ncols, -1.0, t.W + j1, n, false, t.V + j1, n, true, 1.0, C, t.lda, true), s);
+    if (ncols < kNb) {  // a partial last panel: the unused columns must not contribute
+      k_zero_cols<<<(unsigned)std::max(1, (n * (kNb - ncols) + 255) / 256), 256, 0, s>>>(t.V, n, ncols, kNb);
+      k_zero_cols<<<(unsigned)std::max(1, (n * (kNb - ncols) + 255) / 256), 256, 0, s>>>(t.W, n, ncols, kNb);
+      count_launch(2);
+    }
+    k_copy_block<<<(unsigned)std::max(1, std::min(8192, (n * kNb + 255) / 256)), 256, 0, s>>>(t.V, t.W + (int64_t)n * kNb,
+                                                                                           (int64_t)n * kNb);
+    count_launch();
+    gemm(gemm_args(m2, m2, 2 * kNb, -1.0, t.V + j1, n, false, t.W + j1, n, true, 1.0, C, t.lda, true), s);
   }
   if (n >= 1) {
     k_trd_tail<<<1, 32, 0, s>>>(t);
@@ -437,51 +509,60 @@ __global__ void k_orm_vp(const double* __restrict__ A, int64_t lda, int n, int j
     Vp[r + (int64_t)i * n] = x;
   }
 }
-
 // T of the compact WY form I - Vp T Vp^T = H_j0 ... H_j0+nbp-1 (upper
-// triangular), from S = Vp^T Vp: T(i, i) = tau_i,
-// T(0:i, i) = -tau_i T(0:i, 0:i) S(0:i, i).  One CTA of 32 threads.
-__global__ void k_orm_t(const double* __restrict__ S, const double* __restrict__ tau, int nbp, double* T) {
-  __shared__ double Ts[kNb][kNb + 1];
+// triangular, leading dimension kNbBt, in global memory), from
+// S = Vp^T Vp: T(i, i) = tau_i, T(0:i, i) = -tau_i T(0:i, 0:i) S(0:i, i),
+// column by column.  One CTA of kNbBt threads.
+__global__ void __launch_bounds__(kNbBt) k_orm_t(const double* __restrict__ S, const double* __restrict__ tau,
+                                                 int nbp, double* T) {
   const int c = threadIdx.x;
   for (int i = 0; i < nbp; ++i) {
     double x = 0.0;
     if (c < i) {
-      for (int l = c; l < i; ++l) x = fma(Ts[c][l], S[l + i * kNb], x);
+      for (int l = c; l < i; ++l) x = fma(T[c + l * kNbBt], S[l + i * kNbBt], x);
       x = -tau[i] * x;
     }
-    __syncwarp();
-    if (c < nbp) Ts[c][i] = c < i ? x : (c == i ? tau[i] : 0.0);
-    __syncwarp();
+    __syncthreads();
+    if (c < nbp) T[c + i * kNbBt] = c < i ? x : (c == i ? tau[i] : 0.0);
+    __syncthreads();
   }
-  for (int i = 0; i < nbp; ++i)
-    if (c < nbp) T[c + i * kNb] = Ts[c][i];
 }
 
 }  // namespace
 
+// Split factor the backtransformation's scratch is sized for: enough CTAs
+// for four per SM on up to 160 SMs when the k columns alone give too few.
+int orm_max_split(int k) {
+  const int64_t tiles = 2LL * ((std::max(k, 1) + 63) / 64);
+  return (int)std::max<int64_t>(1, std::min<int64_t>(8, (4LL * 160 + tiles - 1) / tiles));
+}
+
 size_t orm_scratch_doubles(int n, int k) {
-  return (size_t)((int64_t)n * kNb + 2 * (int64_t)kNb * kNb + 2 * (int64_t)kNb * std::max(k, 1));
+  const int64_t kk = std::max(k, kNbBt);
+  return (size_t)((int64_t)n * kNbBt + 2LL * kNbBt * kNbBt + 2LL * kNbBt * kk + (int64_t)orm_max_split(k) * kNbBt * kk);
 }
 
 void launch_orm(int n, int k, const double* A, int64_t lda, const double* tau, double* Y, int64_t ldy,
-                double* scratch, cudaStream_t s) {
+                double* scratch, int nsm, cudaStream_t s) {
   if (n <= 2 || k <= 0) return;
+  const int64_t kk = std::max(k, kNbBt);
   double* Vp = scratch;
-  double* S = Vp + (int64_t)n * kNb;
-  double* T = S + kNb * kNb;
-  double* G = T + kNb * kNb;
-  double* G2 = G + (int64_t)kNb * k;
-  const int npanels = (n - 2 + kNb - 1) / kNb;
+  double* S = Vp + (int64_t)n * kNbBt;
+  double* T = S + kNbBt * kNbBt;
+  double* G = T + kNbBt * kNbBt;
+  double* G2 = G + kNbBt * kk;
+  double* part = G2 + kNbBt * kk;
+  const int msplit = orm_max_split(k);
+  const int npanels = (n - 2 + kNbBt - 1) / kNbBt;
   for (int p = npanels - 1; p >= 0; --p) {
-    const int j0 = p * kNb, nbp = std::min(kNb, n - 2 - j0), rows = n - j0 - 1;
+    const int j0 = p * kNbBt, nbp = std::min(kNbBt, n - 2 - j0), rows = n - j0 - 1;
     double* Ysub = Y + (j0 + 1);
-    k_orm_vp<<<std::max(1, std::min(4096, (rows * nbp + 255) / 256)), 256, 0, s>>>(A, lda, n, j0, nbp, Vp);
-    gemm(gemm_args(nbp, nbp, rows, 1.0, Vp, n, true, Vp, n, false, 0.0, S, kNb), s);
-    k_orm_t<<<1, 32, 0, s>>>(S, tau + j0, nbp, T);
-    gemm(gemm_args(nbp, k, rows, 1.0, Vp, n, true, Ysub, ldy, false, 0.0, G, kNb), s);
-    gemm(gemm_args(nbp, k, nbp, 1.0, T, kNb, false, G, kNb, false, 0.0, G2, kNb), s);
-    gemm(gemm_args(rows, k, nbp, -1.0, Vp, n, false, G2, kNb, false, 1.0, Ysub, ldy), s);
+    k_orm_vp<<<std::max(1, std::min(8192, (rows * nbp + 255) / 256)), 256, 0, s>>>(A, lda, n, j0, nbp, Vp);
+    gemm_splitk(gemm_args(nbp, nbp, rows, 1.0, Vp, n, true, Vp, n, false, 0.0, S, kNbBt), part, msplit, nsm, s);
+    k_orm_t<<<1, kNbBt, 0, s>>>(S, tau + j0, nbp, T);
+    gemm_splitk(gemm_args(nbp, k, rows, 1.0, Vp, n, true, Ysub, ldy, false, 0.0, G, kNbBt), part, msplit, nsm, s);
+    gemm(gemm_args(nbp, k, nbp, 1.0, T, kNbBt, false, G, kNbBt, false, 0.0, G2, kNbBt), s);
+    gemm(gemm_args(rows, k, nbp, -1.0, Vp, n, false, G2, kNbBt, false, 1.0, Ysub, ldy), s);
     count_launch(2);
   }
 }
@@ -562,7 +643,11 @@ mrrr_status mrrr_ormtr(mrrr_plan* plan, int n, int k, const double* A, int64_t l
   const DenseLayout L = dense_layout(plan, n, std::min(k, n));
   if (!workspace || ws_bytes < L.total) return MRRR_ERR_WORKSPACE;
   char* w = static_cast<char*>(workspace);
-  launch_orm(n, k, A, lda, tau, Y, ldy, reinterpret_cast<double*>(w + L.scratch), static_cast<cudaStream_t>(stream));
+  int dev = 0, nsm = 152;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return MRRR_ERR_CUDA;
+  launch_orm(n, k, A, lda, tau, Y, ldy, reinterpret_cast<double*>(w + L.scratch), nsm,
+             static_cast<cudaStream_t>(stream));
   return cudaGetLastError() == cudaSuccess ? MRRR_OK : MRRR_ERR_CUDA;
 }
 

@@ -24,15 +24,22 @@ struct GemmArgs {
   double* C;
   int64_t ldc;
   double alpha, beta;
+  int kchunk;       // split-K: CTA z of grid.z sums k in [z kchunk, (z+1) kchunk) (0: all)
+  int64_t cstride;  //   into C + z cstride (the partials, reduced by gemm_splitk)
 };
 
 void gemm(const GemmArgs& g, cudaStream_t s);
+// C = alpha op(A) op(B) + beta C with K split over CTAs when the output has
+// too few tiles to fill the GPU: partial products into `partials` (room for
+// max_split m x n blocks), then summed in a fixed order.
+void gemm_splitk(GemmArgs g, double* partials, int max_split, int nsm, cudaStream_t s);
 
 // op(A), op(B) of column-major matrices (ta / tb: transposed).
 GemmArgs gemm_args(int m, int n, int k, double alpha, const double* A, int64_t lda, bool ta, const double* B,
                    int64_t ldb, bool tb, double beta, double* C, int64_t ldc, bool lower = false);
 
-constexpr int kNb = 32;      // panel width of the blocked algorithms
+constexpr int kNb = 32;      // panel width of the reduction to tridiagonal form
+constexpr int kNbBt = 128;   // reflectors per panel of the backtransformation
 constexpr int kRowCta = 256; // threads of the row-parallel kernels
 
 // Device status of a dense call (first error wins), in the workspace.
@@ -66,7 +73,7 @@ void launch_trd(const TrdArgs& t, cudaStream_t s);
 // below the subdiagonal of the reduced A and tau.
 size_t orm_scratch_doubles(int n, int k);
 void launch_orm(int n, int k, const double* A, int64_t lda, const double* tau, double* Y, int64_t ldy,
-                double* scratch, cudaStream_t s);
+                double* scratch, int nsm, cudaStream_t s);
 
 }  // namespace dense
 }  // namespace mrrr

@@ -21,6 +21,7 @@ namespace dense {
 namespace {
 
 constexpr int kB = 64;  // block of the triangular algorithms
+constexpr int kSplit = 8;  // split-K factor the scratch is sized for
 
 // Unblocked Cholesky of the diagonal block A(k0:k0+bs, k0:k0+bs) in shared
 // memory, right-looking; a pivot that is not positive (or not finite) sets
@@ -128,7 +129,8 @@ void copy(const double* src, int64_t lds, double* dst, int64_t ldd, int rows, in
 
 size_t gen_scratch_doubles(int n, int k) {
   const int64_t nbk = (n + kB - 1) / kB;
-  return (size_t)(nbk * kB * kB + (int64_t)kB * std::max({n, k, 1}) + (int64_t)n * n);
+  const int64_t w = std::max({n, k, 1});
+  return (size_t)(nbk * kB * kB + (int64_t)kB * w * (1 + kSplit) + (int64_t)n * n);
 }
 
 // B (n x n) <- L L^T, lower; scratch: Linv blocks, a kB x n panel buffer.
@@ -154,36 +156,40 @@ void launch_potrf(int n, double* B, int64_t ldb, double* scratch, DenseCtl* ctl,
 
 // X <- L^-1 X (trans = false) or L^-T X (trans = true), X n x k.
 void launch_trsm(int n, int k, const double* L, int64_t ldl, double* X, int64_t ldx, bool trans, double* scratch,
-                 cudaStream_t s) {
+                 int nsm, cudaStream_t s) {
   const int nbk = (n + kB - 1) / kB;
   double* Linv = scratch;
   double* T = Linv + (int64_t)nbk * kB * kB;  // kB x k
+  double* part = T + (int64_t)kB * std::max({n, k, 1});  // split-K partials, kSplit x kB x k
   k_trinv<<<nbk, kB, 0, s>>>(L, ldl, n, Linv);
   count_launch();
   for (int step = 0; step < nbk; ++step) {
     const int I = trans ? nbk - 1 - step : step;
     const int r0 = I * kB, bs = std::min(kB, n - r0), r1 = r0 + bs;
     const double* Li = Linv + (int64_t)I * kB * kB;
+    // the update of block row I has only kB rows: split its depth over CTAs
     if (!trans && r0 > 0)
-      gemm(gemm_args(bs, k, r0, -1.0, L + r0, ldl, false, X, ldx, false, 1.0, X + r0, ldx), s);
+      gemm_splitk(gemm_args(bs, k, r0, -1.0, L + r0, ldl, false, X, ldx, false, 1.0, X + r0, ldx), part, kSplit,
+                  nsm, s);
     if (trans && r1 < n)
-      gemm(gemm_args(bs, k, n - r1, -1.0, L + r1 + (int64_t)r0 * ldl, ldl, true, X + r1, ldx, false, 1.0, X + r0,
-                     ldx),
-           s);
+      gemm_splitk(gemm_args(bs, k, n - r1, -1.0, L + r1 + (int64_t)r0 * ldl, ldl, true, X + r1, ldx, false, 1.0,
+                            X + r0, ldx),
+                  part, kSplit, nsm, s);
     gemm(gemm_args(bs, k, bs, 1.0, Li, kB, trans, X + r0, ldx, false, 0.0, T, kB), s);
     copy(T, kB, X + r0, ldx, bs, k, s);
   }
 }
 
 // A (full symmetric) <- L^-1 A L^-T.
-void launch_sygst(int n, double* A, int64_t lda, const double* L, int64_t ldl, double* scratch, cudaStream_t s) {
+void launch_sygst(int n, double* A, int64_t lda, const double* L, int64_t ldl, double* scratch, int nsm,
+                  cudaStream_t s) {
   const int nbk = (n + kB - 1) / kB;
-  double* M = scratch + (int64_t)nbk * kB * kB + (int64_t)kB * std::max(n, 1);  // n x n
-  launch_trsm(n, n, L, ldl, A, lda, false, scratch, s);  // A <- L^-1 A
+  double* M = scratch + (int64_t)nbk * kB * kB + (int64_t)kB * std::max(n, 1) * (1 + kSplit);  // n x n
+  launch_trsm(n, n, L, ldl, A, lda, false, scratch, nsm, s);  // A <- L^-1 A
   dim3 tb(32, 8), tg((n + 31) / 32, (n + 31) / 32);
   k_transpose<<<tg, tb, 0, s>>>(A, lda, M, n, n);          // M = (L^-1 A)^T = A L^-T
   count_launch();
-  launch_trsm(n, n, L, ldl, M, n, false, scratch, s);      // M <- L^-1 A L^-T
+  launch_trsm(n, n, L, ldl, M, n, false, scratch, nsm, s); // M <- L^-1 A L^-T
   copy(M, n, A, lda, n, n, s);
 }
 
@@ -198,6 +204,13 @@ using namespace mrrr::dense;
 namespace {
 
 size_t galign(size_t x) { return (x + 255) / 256 * 256; }
+
+int device_sms() {
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 0;
+  return nsm;
+}
 
 struct GenLayout {
   size_t ctl, scratch, dense, total, dense_bytes;
@@ -248,7 +261,9 @@ mrrr_status mrrr_sygst(mrrr_plan* plan, int n, double* A, int64_t lda, const dou
   const GenLayout L = gen_layout(plan, n, 0);
   if (!workspace || ws_bytes < L.total) return MRRR_ERR_WORKSPACE;
   char* w = static_cast<char*>(workspace);
-  launch_sygst(n, A, lda, Lf, ldl, reinterpret_cast<double*>(w + L.scratch), static_cast<cudaStream_t>(stream));
+  const int nsm = device_sms();
+  if (nsm <= 0) return MRRR_ERR_CUDA;
+  launch_sygst(n, A, lda, Lf, ldl, reinterpret_cast<double*>(w + L.scratch), nsm, static_cast<cudaStream_t>(stream));
   return cudaGetLastError() == cudaSuccess ? MRRR_OK : MRRR_ERR_CUDA;
 }
 
@@ -260,7 +275,9 @@ mrrr_status mrrr_trsm_lt(mrrr_plan* plan, int n, int k, const double* Lf, int64_
   const GenLayout L = gen_layout(plan, n, std::min(k, n));
   if (!workspace || ws_bytes < L.total) return MRRR_ERR_WORKSPACE;
   char* w = static_cast<char*>(workspace);
-  launch_trsm(n, k, Lf, ldl, X, ldx, true, reinterpret_cast<double*>(w + L.scratch),
+  const int nsm = device_sms();
+  if (nsm <= 0) return MRRR_ERR_CUDA;
+  launch_trsm(n, k, Lf, ldl, X, ldx, true, reinterpret_cast<double*>(w + L.scratch), nsm,
               static_cast<cudaStream_t>(stream));
   return cudaGetLastError() == cudaSuccess ? MRRR_OK : MRRR_ERR_CUDA;
 }

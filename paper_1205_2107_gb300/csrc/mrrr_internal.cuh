@@ -184,6 +184,7 @@ struct Dev {
   double width_scale;   // multiplies the resident lanes when choosing the multisection width
   int fixed_width;      // 0: width from the list length, brackets pooled; else fixed width, no pooling
   int no_orth_fix;      // skip the neighbour orthogonality safeguard (slices)
+  int vec_dd;           // eigenvectors in double-double arithmetic
   int root_side;        // 0 nearer the wanted range, 1 left, 2 right
 };
 

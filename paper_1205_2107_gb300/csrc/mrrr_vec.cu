@@ -273,6 +273,175 @@ __global__ void __launch_bounds__(kVecWarps * 32) k_vectors(Dev v) {
   if (iters) atomicAdd(&v.ctl->twisted_solves, iters);
 }
 
+// ---------------------------------------------------------------------------
+// Double-double eigenvectors (vector_precision = 2).  A value is an
+// unevaluated sum hi + lo with |lo| <= ulp(hi)/2, about 106 bits.  The
+// building blocks are the classical error-free transformations: Knuth's
+// two-sum (s + e = a + b exactly), the FMA two-product (p + e = a b exactly,
+// e = fma(a, b, -p)), Dekker's renormalisation; division takes one FP64
+// quotient, its remainder computed exactly with two-products, and one
+// correction (a Newton step).  Accuracy about 2^-104 relative per operation.
+struct dd {
+  double hi, lo;
+};
+
+__device__ __forceinline__ dd dd_renorm(double s, double e) {  // |s| >= |e|
+  const double h = s + e;
+  return dd{h, e - (h - s)};
+}
+__device__ __forceinline__ dd dd_two_sum(double a, double b) {
+  const double s = a + b, bb = s - a;
+  return dd{s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ dd dd_add(dd x, dd y) {
+  const dd s = dd_two_sum(x.hi, y.hi);
+  const dd t = dd_two_sum(x.lo, y.lo);
+  const dd u = dd_renorm(s.hi, s.lo + t.hi);
+  return dd_renorm(u.hi, u.lo + t.lo);
+}
+__device__ __forceinline__ dd dd_neg(dd x) { return dd{-x.hi, -x.lo}; }
+__device__ __forceinline__ dd dd_sub(dd x, dd y) { return dd_add(x, dd_neg(y)); }
+__device__ __forceinline__ dd dd_mul(dd x, dd y) {
+  const double p = x.hi * y.hi;
+  const double e = fma(x.hi, y.hi, -p);
+  return dd_renorm(p, e + (x.hi * y.lo + x.lo * y.hi));
+}
+__device__ __forceinline__ dd dd_mul_d(dd x, double b) {
+  const double p = x.hi * b;
+  const double e = fma(x.hi, b, -p);
+  return dd_renorm(p, e + x.lo * b);
+}
+__device__ __forceinline__ dd dd_div(dd x, dd y) {
+  const double q1 = x.hi / y.hi;
+  const dd r = dd_sub(x, dd_mul_d(y, q1));  // remainder x - q1 y
+  const double q2 = r.hi / y.hi;
+  return dd_renorm(q1, q2);
+}
+__device__ __forceinline__ dd dd_from(double a) { return dd{a, 0.0}; }
+
+// One double-double twisted factorization of L D L^T - lam I (the rows of
+// the representation, FP64, define it exactly: LD and LLD are recomputed
+// from l and D) and the solve: returns the twist r, gamma_r and ||z||^2; with
+// zc the vector (rounded to FP64) is written.  Scratch: four interleaved
+// arrays (L+ hi/lo, then s and U- hi/lo) of stride nthr.
+__device__ void twisted_dd(const double2* __restrict__ dl, const double2* __restrict__ ul, int m, dd lam,
+                           double pivmin, double* Ah, double* Al, double* Bh, double* Bl, int64_t nthr, double* zc,
+                           int& r_out, dd& gamma_out, dd& norm2_out) {
+  // stationary, top-down: D+ = D + s, L+ = l D / D+, s' = L+ l s - lam
+  dd s = dd_neg(lam);
+  for (int i = 0; i < m - 1; ++i) {
+    const double D = dl[i].x, l = ul[i].x;
+    dd dp = dd_add(dd_from(D), s);
+    if (fabs(dp.hi) < pivmin) dp = dd_from(-pivmin);
+    const dd ld = dd_mul_d(dd_from(l), D);
+    const dd lp = dd_div(ld, dp);
+    Ah[i * nthr] = lp.hi;
+    Al[i * nthr] = lp.lo;
+    Bh[i * nthr] = s.hi;
+    Bl[i * nthr] = s.lo;
+    s = dd_sub(dd_mul(dd_mul_d(lp, l), s), lam);
+  }
+  // progressive, bottom-up: D- = l^2 D + p, t = D / D-, U- = l t, p' = p t - lam
+  dd p = dd_sub(dd_from(dl[m - 1].x), lam);
+  dd g = dd_add(dd_add(s, p), lam);
+  double best = fabs(g.hi);
+  int r = m - 1;
+  dd gamma = g;
+  for (int i = m - 2; i >= 0; --i) {
+    const double D = dl[i].x, l = ul[i].x;
+    const dd lld = dd_mul_d(dd_mul_d(dd_from(l), l), D);
+    dd dm = dd_add(lld, p);
+    if (fabs(dm.hi) < pivmin) dm = dd_from(-pivmin);
+    const dd t = dd_div(dd_from(D), dm);
+    const dd um = dd_mul_d(t, l);
+    p = dd_sub(dd_mul(p, t), lam);
+    g = dd_add(dd_add(dd{Bh[i * nthr], Bl[i * nthr]}, p), lam);
+    if (fabs(g.hi) <= best) {
+      best = fabs(g.hi);
+      r = i;
+      gamma = g;
+    }
+    Bh[i * nthr] = um.hi;
+    Bl[i * nthr] = um.lo;
+  }
+  // solve with z_r = 1
+  dd n2 = dd_from(1.0), z = dd_from(1.0);
+  if (zc) zc[r] = 1.0;
+  for (int i = r - 1; i >= 0; --i) {
+    z = dd_neg(dd_mul(dd{Ah[i * nthr], Al[i * nthr]}, z));
+    n2 = dd_add(n2, dd_mul(z, z));
+    if (zc) zc[i] = z.hi + z.lo;
+  }
+  z = dd_from(1.0);
+  for (int i = r; i < m - 1; ++i) {
+    z = dd_neg(dd_mul(dd{Bh[i * nthr], Bl[i * nthr]}, z));
+    n2 = dd_add(n2, dd_mul(z, z));
+    if (zc) zc[i + 1] = z.hi + z.lo;
+  }
+  r_out = r;
+  gamma_out = gamma;
+  norm2_out = n2;
+}
+
+// Eigenvectors in double-double: per singleton, a twisted factorization at
+// the bisected value (FP64, full accuracy), the Rayleigh-quotient correction
+// lam += gamma_r / ||z||^2 (Eq. errorangle's residual |gamma_r| / ||z||, in
+// double-double), then the twisted factorization and solve at the corrected
+// value; the vector is rounded to FP64 and normalised by k_normalize.  One
+// thread per vector, chunks of 32 slots from the scheduler.
+__global__ void __launch_bounds__(128) k_vectors_dd(Dev v) {
+  const int lane = threadIdx.x & 31;
+  const int64_t tid = gtid(), nthr = gstride();
+  const int64_t nslots = v.ctl->nslots;
+  const int64_t plane = v.vscr_threads * v.vscr_rows;
+  double* Ah = v.vscr + tid;
+  double* Al = Ah + plane;
+  double* Bh = Al + plane;
+  double* Bl = Bh + plane;
+  unsigned long long iters = 0;
+  const long long nchunks = (nslots + 31) / 32;
+  const long long rank = sched_rank(v);
+  bool first = true;
+  for (;;) {
+    const long long chunk = sched_next(v, nchunks, nthr / 32, rank, first);
+    if (chunk < 0) break;
+    const int64_t w = chunk * 32 + lane;
+    if (w >= nslots) continue;
+    const int st = v.state[w];
+    if ((st != SLOT_SINGLETON && st != SLOT_FALLBACK && st != SLOT_TRIVIAL) || v.spos[w] < 0) continue;
+    const int pos = v.spos[w];
+    const Node nd = v.node[v.snode[w]];
+    const Block bk = v.blk[nd.block];
+    const Problem pr = v.prob[bk.prob];
+    const int m = bk.m;
+    double* zc = v.Z ? v.Z + pr.zout + (int64_t)pos * pr.ldz + (bk.row0 - pr.row0) : nullptr;
+    if (st == SLOT_TRIVIAL || m == 1) {
+      v.W[pr.wout + pos] = nd.sigma_abs / pr.scale;
+      if (zc) zc[0] = 1.0;
+      v.znrm2[w] = 1.0;
+      continue;
+    }
+    const double2* rdl = v.rep_dl + nd.rep;
+    const double2* rul = v.rep_ul + nd.rep;
+    dd lam = dd_from(0.5 * (v.lo[w] + v.hi[w]));
+    int r;
+    dd gamma, n2;
+    twisted_dd(rdl, rul, m, lam, nd.pivmin, Ah, Al, Bh, Bl, nthr, nullptr, r, gamma, n2);
+    const dd corr = dd_div(gamma, n2);
+    // the correction stays inside the bisection bracket (else keep the value)
+    const dd lam2 = dd_add(lam, corr);
+    if (lam2.hi >= v.lo[w] && lam2.hi <= v.hi[w]) lam = lam2;
+    twisted_dd(rdl, rul, m, lam, nd.pivmin, Ah, Al, Bh, Bl, nthr, zc, r, gamma, n2);
+    iters += 2;
+    if (!isfinite(n2.hi)) set_status(v.ctl, MRRR_ERR_NOCONV);
+    const dd wabs = dd_add(dd_from(nd.sigma_abs), lam);
+    v.W[pr.wout + pos] = (wabs.hi + wabs.lo) / pr.scale;
+    v.wval[w] = lam.hi;
+    v.znrm2[w] = n2.hi + n2.lo;
+  }
+  if (iters) atomicAdd(&v.ctl->twisted_solves, iters);
+}
+
 // One CTA per output slot: scale the column to unit norm and clear the rows
 // outside its block (problems that split).
 __global__ void k_normalize(Dev v) {
@@ -443,7 +612,10 @@ __global__ void k_fix_order(Dev v) {
 void launch_vectors(const Dev& v, const Grid& g, cudaStream_t s) {
   k_sched_reset<<<1, kSchedSlots, 0, s>>>(v);
   count_launch();
-  k_vectors<<<g.vec_blocks, 128, 0, s>>>(v);
+  if (v.vec_dd)
+    k_vectors_dd<<<g.vec_blocks, 128, 0, s>>>(v);
+  else
+    k_vectors<<<g.vec_blocks, 128, 0, s>>>(v);
   count_launch();
   if (v.Z) {
     k_normalize<<<g.nsm * 16, 256, 0, s>>>(v);
