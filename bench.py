@@ -463,11 +463,11 @@ def run_ours(args, rank: int, world: int):
     mixed = None
     shard = None
     if not args.no_side:
-        side = side_by_side(args, dev, flush)
-        large = large_legs(dev, flush)
-        dense = dense_legs(dev, flush)
-        mixed = mixed_precision_leg(dev, flush)
-        shard = shard_leg(dev, flush)
+        side = _leg(side_by_side, args, dev, flush)
+        large = _leg(large_legs, dev, flush)
+        dense = _leg(dense_legs, dev, flush)
+        mixed = _leg(mixed_precision_leg, dev, flush)
+        shard = _leg(shard_leg, dev, flush)
     clocks = clk.summary()
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -495,6 +495,20 @@ def run_ours(args, rank: int, world: int):
             "stages_ms_direct_launch": stages_direct}
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def _leg(fn, *args):
+    """Run one side leg and return its record with the device memory it
+    peaked at; what it allocated is released before the next one."""
+    import gc
+    import torch
+    torch.cuda.reset_peak_memory_stats()
+    out = fn(*args)
+    gc.collect()
+    torch.cuda.empty_cache()
+    if isinstance(out, dict):
+        out["peak_device_gb"] = torch.cuda.max_memory_allocated() / 2 ** 30
+    return out
 
 
 def verify_solution(d, e, W, Z, seed: int = 0) -> dict:
@@ -689,6 +703,8 @@ def shard_leg(dev, flush, nslices=4):
         plan = api.Plan(dev)
         api.eigh_tridiagonal(dt, et, plan=plan)
         t_full = _time_cuda(lambda: api.eigh_tridiagonal(dt, et, plan=plan, check=False), 1, flush)
+        del plan
+        torch.cuda.empty_cache()
         times, edges, margins = [], [], []
         prev = None
         for sl in range(nslices):

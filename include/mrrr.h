@@ -460,9 +460,12 @@ mrrr_status mrrr_get_profile(const mrrr_plan* plan, mrrr_profile* out);
    denominator of the solver's roofline figures.  Not in the paper:
    measurement support.  kind 0: FP64 FMA (flop/s, 2 per FMA), 1: FP64 tensor
    core MMA m8n8k4 (flop/s), 2: FP64 division (divisions/s), 3: FP32 FMA
-   (flop/s).  Times throughput kernels on every SM with CUDA events on a
+   (flop/s), 4: FP64 FMA warp instructions per second with one active lane
+   per warp.  Times throughput kernels on every SM with CUDA events on a
    stream of its own (best of three, about 0.1-0.2 s in all) and
-   synchronises.  Returns MRRR_ERR_ARG for a bad kind or NULL rate,
+   synchronises.  kind 5 / 6: SM clock cycles of one dependent FP64 FMA /
+   of one dependent FP64 division plus add, one warp alone on the GPU
+   (clock64 around a chain; the legacy stream, synchronous).  Returns MRRR_ERR_ARG for a bad kind or NULL rate,
    MRRR_ERR_CUDA when a launch fails. */
 mrrr_status mrrr_probe_peak(int kind, double* rate);
 

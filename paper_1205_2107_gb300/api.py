@@ -215,7 +215,10 @@ def slice_range(il: int, iu: int, nslices: int, slice_: int) -> tuple[int, int]:
 
 class _SliceCall:
     def __init__(self, plan, n, d, e, il, iu, nslices, slice_, margin, W, Zt):
-        self.__dict__.update(locals())
+        # explicit fields: no reference back to the call object itself, so it
+        # (and the plan and tensors it holds) is freed as soon as it is dropped
+        self.plan, self.n, self.d, self.e, self.il, self.iu = plan, n, d, e, il, iu
+        self.nslices, self.slice_, self.margin, self.W, self.Zt = nslices, slice_, margin, W, Zt
         self.a, self.b = slice_range(il, iu, nslices, slice_)
 
     def grow_margin(self):
@@ -261,7 +264,9 @@ def eigh_tridiagonal_slice(d: torch.Tensor, e: torch.Tensor, il: int | None, iu:
 
 class _BatchedCall:
     def __init__(self, plan, batch, off, d, e, il, iu, W, w_off, Z, z_off, n_total, k_total, n_max):
-        self.__dict__.update(locals())
+        self.plan, self.batch, self.off, self.d, self.e, self.il, self.iu = plan, batch, off, d, e, il, iu
+        self.W, self.w_off, self.Z, self.z_off = W, w_off, Z, z_off
+        self.n_total, self.k_total, self.n_max = n_total, k_total, n_max
 
     def ws_bytes(self):
         return self.plan.workspace_size(self.batch, self.n_total, self.k_total, self.n_max)
@@ -409,13 +414,16 @@ def autotune_batched(d: torch.Tensor, e: torch.Tensor, layout: BatchLayout, *, p
             "best_ms": float(t.best_ms), "default_ms": float(t.default_ms), "configs": int(t.configs)}
 
 
-PEAK_KINDS = {"dfma": 0, "dmma": 1, "ddiv": 2, "ffma": 3}
+PEAK_KINDS = {"dfma": 0, "dmma": 1, "ddiv": 2, "ffma": 3, "dfma_one_lane": 4, "dfma_latency": 5,
+              "ddiv_latency": 6}
 
 
 def probe_peak(kind: str) -> float:
     """Measured peak rate of one unit of the current GPU (mrrr_probe_peak):
     'dfma' and 'dmma' in FP64 flop/s, 'ddiv' in divisions/s, 'ffma' in FP32
-    flop/s."""
+    flop/s, 'dfma_one_lane' in FP64 FMA warp instructions/s with one active
+    lane per warp; 'dfma_latency' and 'ddiv_latency' in SM cycles per
+    dependent step."""
     rate = ctypes.c_double(0.0)
     _lib.check(_lib.load().mrrr_probe_peak(PEAK_KINDS[kind], ctypes.byref(rate)), "mrrr_probe_peak")
     return float(rate.value)

@@ -298,10 +298,13 @@ constexpr int kSymvTile = 64;
 // y = A22 v (A22 = A(j+1:n, j+1:n), lower triangle stored), tile by tile:
 // tile (I, J), J <= I, adds tile v_J to rows of block I and tile^T v_I to
 // rows of block J, into P(I, J, :) and P(J, I, :); a diagonal tile applies
-// its lower triangle both ways.
-__global__ void __launch_bounds__(256) k_trd_symv(TrdArgs t, int j, int i) {
+// its lower triangle both ways.  All 256 threads work: thread (q, t) sums a
+// quarter (16 entries) of row t and of column t, then the quarters are
+// added in a fixed order.  Four CTAs per SM.
+__global__ void __launch_bounds__(256, 4) k_trd_symv(TrdArgs t, int j, int i) {
   __shared__ double tile[kSymvTile][kSymvTile + 1];
   __shared__ double vi[kSymvTile], vj[kSymvTile];
+  __shared__ double rpart[4][kSymvTile], cpart[4][kSymvTile];
   const int m = t.n - j - 1;
   const int T = (m + kSymvTile - 1) / kSymvTile;
   const int64_t b = blockIdx.x;
@@ -311,11 +314,12 @@ __global__ void __launch_bounds__(256) k_trd_symv(TrdArgs t, int j, int i) {
   const int J = (int)(b - (int64_t)I * (I + 1) / 2);
   const int r0 = j + 1 + I * kSymvTile, c0 = j + 1 + J * kSymvTile;
   const int64_t n = t.n;
+  const bool diag = I == J;
   for (int idx = threadIdx.x; idx < kSymvTile * kSymvTile; idx += blockDim.x) {
     const int cc = idx / kSymvTile, rr = idx % kSymvTile;  // rows contiguous in memory
     const int row = r0 + rr, col = c0 + cc;
     double x = 0.0;
-    if (row < t.n && col < t.n && (I != J || rr >= cc)) x = t.A[row + (int64_t)col * t.lda];
+    if (row < t.n && col < t.n && (!diag || rr >= cc)) x = t.A[row + (int64_t)col * t.lda];
     tile[rr][cc] = x;
   }
   if (threadIdx.x < kSymvTile) {
@@ -324,21 +328,27 @@ __global__ void __launch_bounds__(256) k_trd_symv(TrdArgs t, int j, int i) {
     vj[threadIdx.x] = col < t.n ? t.V[col + i * n] : 0.0;
   }
   __syncthreads();
+  const int tt = threadIdx.x & (kSymvTile - 1), q = threadIdx.x >> 6;
+  const int k0 = q * (kSymvTile / 4);
+  double rs = 0.0, cs = 0.0;
+#pragma unroll 4
+  for (int k = k0; k < k0 + kSymvTile / 4; ++k) {
+    rs = fma(tile[tt][k], vj[k], rs);     // row tt of the tile
+    cs = fma(tile[k][tt], diag ? vj[k] : vi[k], cs);  // column tt (on the diagonal: row tt of the upper half)
+  }
+  rpart[q][tt] = rs;
+  cpart[q][tt] = cs;
+  __syncthreads();
   double* P = t.P;
-  if (threadIdx.x < kSymvTile) {  // rows of block I: tile v_J (+ the transpose on the diagonal)
-    const int rr = threadIdx.x;
-    double sum = 0.0;
-    for (int cc = 0; cc < kSymvTile; ++cc) sum = fma(tile[rr][cc], vj[cc], sum);
-    if (I == J) {
-      for (int cc = 0; cc < kSymvTile; ++cc) sum = fma(tile[cc][rr], vj[cc], sum);
-      sum -= tile[rr][rr] * vj[rr];
+  if (threadIdx.x < kSymvTile) {
+    const double r = ((rpart[0][tt] + rpart[1][tt]) + rpart[2][tt]) + rpart[3][tt];
+    const double c = ((cpart[0][tt] + cpart[1][tt]) + cpart[2][tt]) + cpart[3][tt];
+    if (diag) {
+      P[((int64_t)I * T + J) * kSymvTile + tt] = r + c - tile[tt][tt] * vj[tt];
+    } else {
+      P[((int64_t)I * T + J) * kSymvTile + tt] = r;
+      P[((int64_t)J * T + I) * kSymvTile + tt] = c;
     }
-    P[((int64_t)I * T + J) * kSymvTile + rr] = sum;
-  } else if (threadIdx.x < 2 * kSymvTile && I != J) {  // rows of block J: tile^T v_I
-    const int cc = threadIdx.x - kSymvTile;
-    double sum = 0.0;
-    for (int rr = 0; rr < kSymvTile; ++rr) sum = fma(tile[rr][cc], vi[rr], sum);
-    P[((int64_t)J * T + I) * kSymvTile + cc] = sum;
   }
 }
 

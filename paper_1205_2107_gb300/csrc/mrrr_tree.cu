@@ -1,7 +1,8 @@
 // mrrr_tree.cu -- one level of the representation tree (paper Sec. 3.1.1):
 // classification of the eigenvalues of each node into singletons and
-// clusters by relative gap (singleton iff relgap > tol, tol = 1e-3, gaps and
-// magnitudes in the node's shifted coordinates), a child representation
+// clusters by relative gap (singleton iff relgap > tol, tol = max(gap_tol,
+// 1/m) with gap_tol = 1e-4 by default, gaps and magnitudes in the node's
+// shifted coordinates), a child representation
 // Lc Dc Lc^T = L D L^T - sigma_c I for every cluster (stationary qd
 // transform, sigma_c at an end of the cluster), and refinement of the
 // cluster's eigenvalues with respect to the child by bisection.

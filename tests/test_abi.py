@@ -96,6 +96,15 @@ def test_static_entry_checks_its_arguments_first(lib):
     assert lib.mrrr_eigenvalues_static(5, p, p, 2, 6, p, None) == _lib.ERR_ARG
 
 
+def test_probe_checks_its_arguments_first(lib):
+    """mrrr_probe_peak rejects an unknown kind or a NULL rate before any
+    device call (kinds 0..6)."""
+    rate = ctypes.c_double(-1.0)
+    assert lib.mrrr_probe_peak(7, ctypes.byref(rate)) == _lib.ERR_ARG
+    assert lib.mrrr_probe_peak(-1, ctypes.byref(rate)) == _lib.ERR_ARG
+    assert lib.mrrr_probe_peak(0, None) == _lib.ERR_ARG
+
+
 C_CLIENT = r"""
 #include <stdio.h>
 #include <string.h>

@@ -156,3 +156,29 @@ def test_info_raises_when_the_status_read_fails(monkeypatch):
     monkeypatch.setattr(_lib, "load", lambda *a, **k: FakeLib(_lib.ERR_ARG, _lib.ERR_ARG))
     assert plan.info()["status"] == _lib.ERR_ARG
     plan._h = None  # nothing for __del__ to destroy
+
+
+
+def test_call_objects_hold_no_reference_cycle(monkeypatch):
+    """The per-call objects of the solver entries hold the plan (and with it
+    its workspace) and the output tensors: dropping one must free it by
+    reference counting, without waiting for the cyclic collector (a cycle
+    kept several plans' workspaces alive at once)."""
+    import gc
+    import weakref
+
+    from paper_1205_2107_gb300 import api
+
+    monkeypatch.setattr(api, "slice_range", lambda il, iu, ns, s: (1, 4))
+    t = torch.zeros(4, dtype=torch.float64)
+    gc.disable()
+    try:
+        for make in (lambda: api._SteinCall(_FakePlan([]), 4, t, t, 1, 4, t, t),
+                     lambda: api._SliceCall(_FakePlan([]), 4, t, t, 1, 4, 2, 0, 32, t, t),
+                     lambda: api._BatchedCall(_FakePlan([]), 1, t, t, t, t, t, t, t, t, t, 4, 4, 4)):
+            o = make()
+            r = weakref.ref(o)
+            del o
+            assert r() is None
+    finally:
+        gc.enable()
