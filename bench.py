@@ -705,7 +705,7 @@ def shard_leg(dev, flush, nslices=4):
         t_full = _time_cuda(lambda: api.eigh_tridiagonal(dt, et, plan=plan, check=False), 1, flush)
         del plan
         torch.cuda.empty_cache()
-        times, edges, margins = [], [], []
+        times, edges, margins, stages = [], [], [], []
         prev = None
         for sl in range(nslices):
             splan = api.Plan(dev)
@@ -718,8 +718,10 @@ def shard_leg(dev, flush, nslices=4):
                     break
                 m *= 4
             margins.append(m)
+            splan.set_timing(True)
             times.append(_time_cuda(lambda: api.eigh_tridiagonal_slice(dt, et, 1, n, nslices, sl, margin=m,
                                                                       plan=splan, check=False), 1, flush))
+            stages.append({k: round(v, 2) for k, v in splan.profile()["stages"].items() if v >= 0.05})
             if prev is not None:  # last 512 columns of the previous slice against the first 512 of this one
                 G = prev.t() @ Z[:, :512]
                 edges.append(float(G.abs().max()) / (n * 2.0 ** -53))
@@ -728,16 +730,19 @@ def shard_leg(dev, flush, nslices=4):
             torch.cuda.empty_cache()
         out[name] = {"n": n, "slices": nslices, "full_ms": t_full, "slice_ms": times, "job_ms": max(times),
                      "speedup_over_one_gpu": t_full / max(times), "efficiency": t_full / max(times) / nslices,
-                     "margins": margins, "boundary_orthogonality_n_eps": edges}
+                     "margins": margins, "boundary_orthogonality_n_eps": edges,
+                     "slice_stages_ms": stages}
     out["note"] = "slices timed one after the other on one GPU; a job on as many GPUs takes the slowest slice"
     return out
 
 
 def mixed_precision_leg(dev, flush):
-    """Eigenvectors in double-double (vector_precision = 2) against FP64 on
-    the same tridiagonal: uniform random n=20000 (seed 1205), all
-    eigenpairs; time and orthogonality (sampled: all columns against 1,024
-    seeded ones and a +-256 band)."""
+    """Eigenvectors in double-double (vector_precision = 2), and singletons
+    bisected to 2^-36 then corrected once by the Rayleigh quotient
+    (singleton_rq = 1), against the FP64 default on the same tridiagonal:
+    uniform random n=20000 (seed 1205), all eigenpairs; time and
+    orthogonality (sampled: all columns against 1,024 seeded ones and a
+    +-256 band)."""
     import torch
     from paper_1205_2107_gb300 import api
     d, e = inputs.uniform(20000, 1205)
@@ -745,8 +750,9 @@ def mixed_precision_leg(dev, flush):
     et = torch.tensor(np.append(e, 0.0), device=dev)
     n = len(d)
     out = {}
-    for name, prec in (("fp64", 1), ("double_double", 2)):
-        plan = api.Plan(dev, vector_precision=prec)
+    for name, opts in (("fp64", {}), ("fp64_rayleigh_quotient_1", {"singleton_rq": 1}),
+                       ("double_double", {"vector_precision": 2})):
+        plan = api.Plan(dev, **opts)
         W, Z = api.eigh_tridiagonal(dt, et, plan=plan)
         ms = _time_cuda(lambda: api.eigh_tridiagonal(dt, et, plan=plan, check=False), 2, flush)
         acc = verify_solution(dt, et, W, Z)

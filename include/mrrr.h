@@ -112,7 +112,16 @@ typedef struct mrrr_options {
                               then eigenvectors of one matrix to about eps^2 / relgap, so
                               orthogonality improves (Sec. 2.3, higher internal precision);
                               several times the FP64 stage's time */
-  int reserved_[5];        /* zero */
+  int singleton_rq;        /* Rayleigh-quotient correction of singletons (Sec. 3.1.1: the
+                              vector stage may improve an eigenvalue): 0 (default) bisects
+                              every singleton to full relative accuracy (2 eps) and takes
+                              one twisted factorization; k = 1..4 bisects only to 2^-36
+                              relative, then takes k + 1 twisted factorizations, each
+                              moving lambda by the Rayleigh quotient gamma_r / ||z||^2 of
+                              the last (kept inside the bisection bracket); the vector
+                              is the last one's and lambda its Rayleigh quotient.  FP64
+                              vectors only (vector_precision 1) */
+  int reserved_[4];        /* zero */
 } mrrr_options;
 
 /* Counters reported by mrrr_get_status (device values after the last solve). */

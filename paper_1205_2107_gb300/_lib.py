@@ -37,7 +37,8 @@ class Options(ctypes.Structure):
                 ("vec_blocks_per_sm", c_int), ("use_graph", c_int), ("max_nodes", c_int64),
                 ("pool_rows", c_int64), ("cluster_rtol", c_double), ("root_perturb", c_double),
                 ("width_scale", c_double), ("multisection_width", c_int), ("root_side", c_int),
-                ("vector_precision", c_int), ("reserved_", c_int * 5)]
+                ("vector_precision", c_int), ("singleton_rq", c_int),
+                ("reserved_", c_int * 4)]
 
 
 class Info(ctypes.Structure):

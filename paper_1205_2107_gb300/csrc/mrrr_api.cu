@@ -290,6 +290,7 @@ Dev make_dev(const mrrr_plan* p, const Layout& L, void* ws, int batch, const dou
   v.fixed_width = o.multisection_width;
   v.root_side = o.root_side;
   v.vec_dd = o.vector_precision == 2;
+  v.rq_steps = o.singleton_rq;
   return v;
 }
 
@@ -573,11 +574,13 @@ mrrr_status mrrr_plan_create(mrrr_plan** plan, const mrrr_options* opt) {
     if (opt->multisection_width > 0) o.multisection_width = opt->multisection_width;
     if (opt->root_side > 0) o.root_side = opt->root_side;
     if (opt->vector_precision > 0) o.vector_precision = opt->vector_precision;
+    if (opt->singleton_rq != 0) o.singleton_rq = opt->singleton_rq;
   }
   const int mw = o.multisection_width;
   if (mw < 0 || mw > 32 || (mw & (mw - 1)) != 0 || o.root_side < 0 || o.root_side > 2 ||
-      o.vector_precision < 0 || o.vector_precision > 2)
+      o.vector_precision < 0 || o.vector_precision > 2 || o.singleton_rq < 0 || o.singleton_rq > 4)
     return MRRR_ERR_ARG;
+  if (o.singleton_rq > 0 && o.vector_precision == 2) return MRRR_ERR_NOTIMPL;
   if (o.gap_tol >= 1.0 || o.classify_rtol >= 0.25 || o.threads_per_block % 32 != 0) return MRRR_ERR_ARG;
   int dev = 0, nsm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return MRRR_ERR_CUDA;

@@ -30,7 +30,8 @@
 //              widened until it holds, then bisected to rtol;
 //   FINAL      singletons on their node's representation, to full relative
 //              accuracy (the interval can no longer be split), so that one
-//              twisted factorization gives the vector.
+//              twisted factorization gives the vector (with Rayleigh-quotient
+//              corrections in the vector stage: to 2^-36 only).
 #include <cmath>
 
 #include "mrrr_launch.h"
@@ -68,9 +69,16 @@ __device__ __forceinline__ bool slot_in_mode(const Dev& v, int64_t w, int level_
   return true;
 }
 
+// Singletons whose vectors take Rayleigh-quotient corrections stop at 2^-36
+// relative: one correction squares the relative error over the relative gap
+// (>= 1e-4), which lands below eps.  Eigenvalues without vectors are bisected
+// to full accuracy whatever the option.
+constexpr double kRqRtol = 0x1p-36;
+
 template <int MODE>
 __device__ __forceinline__ double mode_rtol(const Dev& v) {
-  return MODE == MODE_ROOT || MODE == MODE_REFINE ? v.rtol : MODE == MODE_FINAL ? 2.0 * kEps : v.rtol_cluster;
+  if (MODE == MODE_FINAL) return v.rq_steps > 0 && v.Z ? kRqRtol : 2.0 * kEps;
+  return MODE == MODE_ROOT || MODE == MODE_REFINE ? v.rtol : v.rtol_cluster;
 }
 
 constexpr double kLongBits = 12.0;  // bisection steps above which an interval is "long"

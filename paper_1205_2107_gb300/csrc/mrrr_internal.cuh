@@ -113,6 +113,7 @@ struct Ctl {
   unsigned long long sched_cleanup;  //   sweep over ranked chunks nobody claimed
   unsigned long long stage_ns[16];  // per-stage GPU time from device-clock marks (graph solves)
   unsigned long long t_last;        // global timer at the last mark
+  long long orth_runs;              // runs of linked eigenvectors found by the safeguard
 };
 
 // Indices of Ctl::diag (mirrored in mrrr_info.diag).
@@ -185,6 +186,7 @@ struct Dev {
   int fixed_width;      // 0: width from the list length, brackets pooled; else fixed width, no pooling
   int no_orth_fix;      // skip the neighbour orthogonality safeguard (slices)
   int vec_dd;           // eigenvectors in double-double arithmetic
+  int rq_steps;         // Rayleigh-quotient corrections of singletons (0: full bisection)
   int root_side;        // 0 nearer the wanted range, 1 left, 2 right
 };
 

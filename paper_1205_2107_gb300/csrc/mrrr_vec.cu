@@ -6,7 +6,9 @@
 // split problems.
 //
 // The eigenvalue comes in bisected to full relative accuracy (the interval
-// engine's FINAL mode), so a single twisted factorization suffices.
+// engine's FINAL mode), so a single twisted factorization suffices; with
+// Rayleigh-quotient corrections (option singleton_rq) it comes in to 2^-36
+// and each correction takes one more factorization.
 // Twisted factorization of L D L^T - lambda I at twist index r:
 //   stationary (top-down)   s_1 = -lambda, D+_i = D_i + s_i,
 //                           L+_i = LD_i / D+_i, s_{i+1} = L+_i l_i s_i - lambda
@@ -209,6 +211,7 @@ __device__ void twisted_warp(const VecLane& q, double* __restrict__ A, double* _
   norm2_out = n2;
 }
 
+template <bool RQ>
 __global__ void __launch_bounds__(kVecWarps * 32) k_vectors(Dev v) {
   __shared__ double stage_all[kVecWarps][kStageRows][33];
   const int lane = threadIdx.x & 31;
@@ -261,9 +264,21 @@ __global__ void __launch_bounds__(kVecWarps * 32) k_vectors(Dev v) {
     if (!__any_sync(0xffffffffu, q.m > 0)) continue;
     int r;
     double gamma, n2;
-    twisted_warp(q, A, B, nthr, stage, lane, r, gamma, n2);
+    // Rayleigh-quotient corrections (rq_steps > 0): z^T (L D L^T - lam I) z =
+    // gamma_r z_r with z_r = 1, so lam + gamma_r / ||z||^2 is the Rayleigh
+    // quotient of the last vector; each new value, kept inside the
+    // bisection bracket, gets a new twisted factorization, and the last
+    // one's quotient is the eigenvalue.
+    const double blo = (RQ && q.m > 0) ? v.lo[w] : 0.0;
+    const double bhi = (RQ && q.m > 0) ? v.hi[w] : 0.0;
+    for (int it = 0;; ++it) {
+      twisted_warp(q, A, B, nthr, stage, lane, r, gamma, n2);
+      if (!RQ) break;
+      if (q.m > 0) q.lam = fmin(fmax(q.lam + gamma / n2, blo), bhi);
+      if (it >= v.rq_steps) break;
+    }
     if (q.m > 0) {
-      ++iters;
+      iters += 1 + v.rq_steps;
       if (!isfinite(n2)) set_status(v.ctl, MRRR_ERR_NOCONV);
       v.W[pr.wout + pos] = (nd.sigma_abs + q.lam) / pr.scale;
       v.wval[w] = q.lam;
@@ -485,19 +500,15 @@ __device__ __forceinline__ bool slot_has_column(const Dev& v, int64_t w) {
   return (st == SLOT_SINGLETON || st == SLOT_FALLBACK || st == SLOT_TRIVIAL) && v.spos[w] >= 0;
 }
 
-__device__ __forceinline__ double warp_dot(const double* a, const double* b, int m, int lane) {
-  double s = 0.0;
-  for (int i = lane; i < m; i += 32) s = fma(a[i], b[i], s);
-  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  return s;
-}
-
 // One warp per slot: link[w] = largest k <= kOrthNeighbors with
-// |z_w^T z_{w+k}| above the threshold (0 if none).  The per-slot index array
-// sj (no longer needed once the eigenvalues are final) holds the links.
-__global__ void k_orth_links(Dev v) {
+// |z_w^T z_{w+k}| above the threshold (0 if none).  The warp reads its
+// column once and the kOrthNeighbors following ones side by side (one
+// accumulator per neighbour, lanes over rows); the per-slot index array sj
+// (no longer needed once the eigenvalues are final) holds the links.
+__global__ void __launch_bounds__(256) k_orth_links(Dev v) {
   const int lane = threadIdx.x & 31;
   const int64_t nslots = v.ctl->nslots;
+  if (gtid() == 0) v.ctl->orth_runs = 0;
   for (int64_t w = gtid() >> 5; w < nslots; w += gstride() >> 5) {
     int link = 0;
     if (slot_has_column(v, w)) {
@@ -506,26 +517,42 @@ __global__ void k_orth_links(Dev v) {
       const int64_t last = bk.slot0 + (bk.je - bk.js);
       const double thr = kOrthFixTol * bk.m * kEps;
       const double* zw = slot_column(v, w, bk, q);
-      for (int k = 1; k <= kOrthNeighbors && w + k <= last; ++k) {
-        if (!slot_has_column(v, w + k)) continue;
-        const double dot = warp_dot(zw, slot_column(v, w + k, bk, q), bk.m, lane);
-        if (fabs(dot) > thr) link = k;
+      const double* zk[kOrthNeighbors];
+#pragma unroll
+      for (int k = 0; k < kOrthNeighbors; ++k) {
+        const int64_t t = w + 1 + k;
+        zk[k] = (t <= last && slot_has_column(v, t)) ? slot_column(v, t, bk, q) : nullptr;
+      }
+      double acc[kOrthNeighbors];
+#pragma unroll
+      for (int k = 0; k < kOrthNeighbors; ++k) acc[k] = 0.0;
+      for (int i = lane; i < bk.m; i += 32) {
+        const double a = zw[i];
+#pragma unroll
+        for (int k = 0; k < kOrthNeighbors; ++k)
+          if (zk[k]) acc[k] = fma(a, zk[k][i], acc[k]);
+      }
+#pragma unroll
+      for (int k = 0; k < kOrthNeighbors; ++k) {
+        double s = acc[k];
+        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (zk[k] && fabs(s) > thr) link = k + 1;
       }
     }
     if (lane == 0) v.sj[w] = link;
   }
 }
 
-// One warp per block: runs of linked slots, each re-orthogonalised in order.
-__global__ void k_orth_fix(Dev v) {
+// One warp per block: the runs of linked slots (a slot and every slot its
+// link reaches, closed under reaching), appended to the run list as
+// (first slot, last slot) pairs in the engine's work list, free by now.
+__global__ void k_orth_runs(Dev v) {
   const int lane = threadIdx.x & 31;
   const int nblocks = v.ctl->nblocks;
   for (int64_t b = gtid() >> 5; b < nblocks; b += gstride() >> 5) {
     const Block bk = v.blk[b];
     if (bk.m < 2 || bk.je < bk.js) continue;
-    const Problem q = v.prob[bk.prob];
     const int64_t s0 = bk.slot0, s1 = bk.slot0 + (bk.je - bk.js);
-    const int m = bk.m;
     int64_t w = s0;
     while (w <= s1) {
       // next linked slot at or after w, 32 slots per step
@@ -539,25 +566,63 @@ __global__ void k_orth_fix(Dev v) {
       int64_t reach = start + v.sj[start];
       for (int64_t t = start + 1; t <= reach && t <= s1; ++t) reach = max(reach, t + (int64_t)v.sj[t]);
       reach = min(reach, s1);
-      if (lane == 0) diag(v.ctl, DIAG_ORTH_FIX);
-      for (int64_t c = start + 1; c <= reach; ++c) {
-        if (!slot_has_column(v, c)) continue;
-        double* zc = const_cast<double*>(slot_column(v, c, bk, q));
-        for (int pass = 0; pass < 2; ++pass) {
-          for (int64_t p = start; p < c; ++p) {
-            if (!slot_has_column(v, p)) continue;
-            const double* zp = slot_column(v, p, bk, q);
-            const double dot = warp_dot(zc, zp, m, lane);
-            for (int i = lane; i < m; i += 32) zc[i] = fma(-dot, zp[i], zc[i]);
-            __syncwarp();
-          }
+      if (lane == 0) {
+        const long long r = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(&v.ctl->orth_runs), 1ULL);
+        if (2 * r + 1 < v.max_list) {
+          v.ilist[2 * r] = start;
+          v.ilist[2 * r + 1] = reach;
         }
-        const double n2 = warp_dot(zc, zc, m, lane);
-        const double sc = n2 > 0.0 ? 1.0 / sqrt(n2) : 1.0;
-        for (int i = lane; i < m; i += 32) zc[i] *= sc;
-        __syncwarp();
+        diag(v.ctl, DIAG_ORTH_FIX);
       }
       w = reach + 1;
+    }
+  }
+}
+
+constexpr int kFixThreads = 256;
+
+// CTA-wide sum (all threads get it); red holds kFixThreads / 32 doubles.
+__device__ __forceinline__ double cta_sum(double x, double* red) {
+  for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) red[wid] = x;
+  __syncthreads();
+  double s = 0.0;
+  for (int k = 0; k < kFixThreads / 32; ++k) s += red[k];
+  return s;
+}
+
+// One CTA per run: each column after the run's first is re-orthogonalised
+// against the earlier ones, in eigenvalue order (modified Gram-Schmidt,
+// twice), then normalised.
+__global__ void __launch_bounds__(kFixThreads) k_orth_fix(Dev v) {
+  __shared__ double red[kFixThreads / 32];
+  const long long nruns = min(v.ctl->orth_runs, (long long)(v.max_list / 2));
+  for (long long r = blockIdx.x; r < nruns; r += gridDim.x) {
+    const int64_t start = v.ilist[2 * r], reach = v.ilist[2 * r + 1];
+    const Block bk = v.blk[v.node[v.snode[start]].block];
+    const Problem q = v.prob[bk.prob];
+    const int m = bk.m;
+    for (int64_t c = start + 1; c <= reach; ++c) {
+      if (!slot_has_column(v, c)) continue;
+      double* zc = const_cast<double*>(slot_column(v, c, bk, q));
+      for (int pass = 0; pass < 2; ++pass) {
+        for (int64_t p = start; p < c; ++p) {
+          if (!slot_has_column(v, p)) continue;
+          const double* zp = slot_column(v, p, bk, q);
+          double part = 0.0;
+          for (int i = threadIdx.x; i < m; i += kFixThreads) part = fma(zc[i], zp[i], part);
+          const double dot = cta_sum(part, red);
+          for (int i = threadIdx.x; i < m; i += kFixThreads) zc[i] = fma(-dot, zp[i], zc[i]);
+        }
+      }
+      double part = 0.0;
+      for (int i = threadIdx.x; i < m; i += kFixThreads) part = fma(zc[i], zc[i], part);
+      const double n2 = cta_sum(part, red);
+      const double sc = n2 > 0.0 ? 1.0 / sqrt(n2) : 1.0;
+      for (int i = threadIdx.x; i < m; i += kFixThreads) zc[i] *= sc;
+      __syncthreads();
     }
   }
 }
@@ -566,43 +631,60 @@ __global__ void k_orth_fix(Dev v) {
 // midpoints, and near-ties across blocks may leave W slightly out of order;
 // in any problem, eigenvalues equal to the last bit that were finished on
 // different nodes (sigma_abs + local value, each rounded) can come out one or
-// two ulps out of order.  Odd-even transposition passes (one CTA per problem)
-// restore ascending W, moving the columns of Z along; they stop after two
-// passes without a swap.
-__global__ void k_fix_order(Dev v) {
-  __shared__ int swapped;
+// two ulps out of order.  One CTA per problem: a sweep over all of W finds
+// whether any neighbours are out of order (the usual answer is no); if so,
+// odd-even transposition passes with every thread on its own pairs swap the
+// values and queue the swapped pairs, whose columns of Z the warps then swap;
+// the passes stop after two without a swap.
+constexpr int kSwapQueue = 512;
+
+__global__ void __launch_bounds__(kFixThreads) k_fix_order(Dev v) {
+  __shared__ int nq;
+  __shared__ int64_t queue[kSwapQueue];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  constexpr int nw = kFixThreads / 32;
   for (int64_t p = blockIdx.x; p < v.batch; p += gridDim.x) {
     const Problem q = v.prob[p];
     if (q.k < 2) continue;
     double* W = v.W + q.wout;
+    int bad = 0;
+    for (int64_t i = threadIdx.x; i + 1 < q.k; i += kFixThreads) bad |= W[i] > W[i + 1];
+    if (!__syncthreads_or(bad)) continue;
     int quiet = 0;
     for (int pass = 0; pass < 2 * q.k + 2 && quiet < 2; ++pass) {
-      if (threadIdx.x == 0) swapped = 0;
-      __syncthreads();
-      const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-      for (int64_t i = (pass & 1) + 2 * (int64_t)wid; i + 1 < q.k; i += 2 * (int64_t)nw) {
-        double a = W[i], b = W[i + 1];
-        if (a > b) {
-          if (lane == 0) {
-            W[i] = b;
-            W[i + 1] = a;
-            swapped = 1;
-          }
-          if (v.Z) {
-            double* ca = v.Z + q.zout + i * q.ldz;
-            double* cb = ca + q.ldz;
-            for (int64_t r = lane; r < q.n; r += 32) {
-              double t = ca[r];
-              ca[r] = cb[r];
-              cb[r] = t;
+      int swapped = 0;
+      for (int64_t base = (pass & 1); base + 1 < q.k; base += 2 * (int64_t)kSwapQueue) {
+        // a round of up to kSwapQueue pairs: swap values, queue the pairs
+        if (threadIdx.x == 0) nq = 0;
+        __syncthreads();
+        for (int u = 0; u < kSwapQueue / kFixThreads; ++u) {
+          const int64_t i = base + 2 * ((int64_t)u * kFixThreads + threadIdx.x);
+          if (i + 1 < q.k) {
+            const double a = W[i], b = W[i + 1];
+            if (a > b) {
+              W[i] = b;
+              W[i + 1] = a;
+              queue[atomicAdd(&nq, 1)] = i;
             }
           }
         }
-        __syncwarp();
+        __syncthreads();
+        const int cnt = nq;
+        swapped |= cnt > 0;
+        if (v.Z) {
+          for (int t = wid; t < cnt; t += nw) {
+            double* ca = v.Z + q.zout + queue[t] * q.ldz;
+            double* cb = ca + q.ldz;
+            for (int64_t r = lane; r < q.n; r += 32) {
+              const double x = ca[r];
+              ca[r] = cb[r];
+              cb[r] = x;
+            }
+          }
+        }
+        __syncthreads();
       }
-      __syncthreads();
       quiet = swapped ? 0 : quiet + 1;
-      __syncthreads();
     }
   }
 }
@@ -614,8 +696,10 @@ void launch_vectors(const Dev& v, const Grid& g, cudaStream_t s) {
   count_launch();
   if (v.vec_dd)
     k_vectors_dd<<<g.vec_blocks, 128, 0, s>>>(v);
+  else if (v.rq_steps > 0)
+    k_vectors<true><<<g.vec_blocks, 128, 0, s>>>(v);
   else
-    k_vectors<<<g.vec_blocks, 128, 0, s>>>(v);
+    k_vectors<false><<<g.vec_blocks, 128, 0, s>>>(v);
   count_launch();
   if (v.Z) {
     k_normalize<<<g.nsm * 16, 256, 0, s>>>(v);
@@ -623,11 +707,13 @@ void launch_vectors(const Dev& v, const Grid& g, cudaStream_t s) {
     if (!v.no_orth_fix) {
       k_orth_links<<<g.nsm * 16, 256, 0, s>>>(v);
       count_launch();
-      k_orth_fix<<<g.nsm * 4, 128, 0, s>>>(v);
+      k_orth_runs<<<g.nsm, 128, 0, s>>>(v);
+      count_launch();
+      k_orth_fix<<<g.nsm * 2, kFixThreads, 0, s>>>(v);
       count_launch();
     }
   }
-  k_fix_order<<<g.nsm, 256, 0, s>>>(v);
+  k_fix_order<<<g.nsm, kFixThreads, 0, s>>>(v);
   count_launch();
 }
 

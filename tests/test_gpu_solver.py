@@ -208,3 +208,44 @@ def test_two_by_two_subsets():
     d, e = np.array([1.0, 3.0]), np.array([2.0])
     for il, iu in [(1, 1), (2, 2), (1, 2)]:
         assert_parity(d, e, il, iu)
+
+
+# Rayleigh-quotient corrections of singletons (option singleton_rq): the same
+# parity bar as the full-bisection default, on the families with clusters
+# (Wilkinson, glued) and without, all eigenpairs and a subset.
+RQ_CASES = {
+    "uniform_500": lambda: inputs.uniform(500, 77),
+    "wilkinson_201": lambda: inputs.wilkinson_plus(201),
+    "glued_x10": lambda: inputs.glued_wilkinson(10),
+    "toeplitz_300": lambda: inputs.toeplitz(300),
+    "clement_150": lambda: inputs.clement(150),
+}
+
+
+@pytest.mark.parametrize("steps", [1, 2])
+@pytest.mark.parametrize("case", sorted(RQ_CASES))
+def test_singleton_rayleigh_quotient_correction(case, steps):
+    d, e = RQ_CASES[case]()
+    plan = api.Plan(singleton_rq=steps)
+    assert_parity(d, e, plan=plan)
+    n = len(d)
+    assert_parity(d, e, n // 4 + 1, n // 2, plan=plan)
+    info = plan.info()
+    assert info["status"] == 0
+
+
+def test_singleton_rq_takes_one_more_factorization_per_step():
+    d, e = inputs.uniform(400, 5)
+    counts = []
+    for steps in (0, 1, 2):
+        plan = api.Plan(singleton_rq=steps)
+        solve(d, e, plan=plan)
+        counts.append(plan.info()["twisted_solves"])
+    assert counts[1] == 2 * counts[0] and counts[2] == 3 * counts[0]
+
+
+def test_singleton_rq_options_are_checked():
+    with pytest.raises(_lib.MrrrError):
+        api.Plan(singleton_rq=5)
+    with pytest.raises(_lib.MrrrError):
+        api.Plan(singleton_rq=1, vector_precision=2)
