@@ -737,9 +737,10 @@ def shard_leg(dev, flush, nslices=4):
 
 
 def mixed_precision_leg(dev, flush):
-    """Eigenvectors in double-double (vector_precision = 2), and singletons
-    bisected to 2^-36 then corrected once by the Rayleigh quotient
-    (singleton_rq = 1), against the FP64 default on the same tridiagonal:
+    """The FP64 default (singletons bisected to 2^-36, then one
+    Rayleigh-quotient correction: singleton_rq = 1) against singletons
+    bisected to full accuracy (singleton_rq = -1) and against eigenvectors in
+    double-double (vector_precision = 2), on the same tridiagonal:
     uniform random n=20000 (seed 1205), all eigenpairs; time and
     orthogonality (sampled: all columns against 1,024 seeded ones and a
     +-256 band)."""
@@ -750,7 +751,7 @@ def mixed_precision_leg(dev, flush):
     et = torch.tensor(np.append(e, 0.0), device=dev)
     n = len(d)
     out = {}
-    for name, opts in (("fp64", {}), ("fp64_rayleigh_quotient_1", {"singleton_rq": 1}),
+    for name, opts in (("fp64_full_bisection", {"singleton_rq": -1}), ("fp64", {}),
                        ("double_double", {"vector_precision": 2})):
         plan = api.Plan(dev, **opts)
         W, Z = api.eigh_tridiagonal(dt, et, plan=plan)

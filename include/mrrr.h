@@ -113,14 +113,15 @@ typedef struct mrrr_options {
                               orthogonality improves (Sec. 2.3, higher internal precision);
                               several times the FP64 stage's time */
   int singleton_rq;        /* Rayleigh-quotient correction of singletons (Sec. 3.1.1: the
-                              vector stage may improve an eigenvalue): 0 (default) bisects
-                              every singleton to full relative accuracy (2 eps) and takes
-                              one twisted factorization; k = 1..4 bisects only to 2^-36
-                              relative, then takes k + 1 twisted factorizations, each
-                              moving lambda by the Rayleigh quotient gamma_r / ||z||^2 of
-                              the last (kept inside the bisection bracket); the vector
-                              is the last one's and lambda its Rayleigh quotient.  FP64
-                              vectors only (vector_precision 1) */
+                              vector stage may improve an eigenvalue): k = 1..4 (default 1)
+                              bisects each singleton to 2^-36 relative only, then takes
+                              k + 1 twisted factorizations, each moving lambda by the
+                              Rayleigh quotient gamma_r / ||z||^2 of the last (kept inside
+                              the bisection bracket); the vector is the last one's and
+                              lambda its Rayleigh quotient.  -1: no correction, every
+                              singleton bisected to full relative accuracy (2 eps) and one
+                              twisted factorization.  Ignored with vector_precision 2
+                              (which bisects fully and corrects in double-double) */
   int reserved_[4];        /* zero */
 } mrrr_options;
 

@@ -290,7 +290,8 @@ Dev make_dev(const mrrr_plan* p, const Layout& L, void* ws, int batch, const dou
   v.fixed_width = o.multisection_width;
   v.root_side = o.root_side;
   v.vec_dd = o.vector_precision == 2;
-  v.rq_steps = o.singleton_rq;
+  // double-double vectors take their own correction from a fully bisected value
+  v.rq_steps = o.vector_precision == 2 || o.singleton_rq < 0 ? 0 : o.singleton_rq;
   return v;
 }
 
@@ -548,6 +549,7 @@ mrrr_status mrrr_options_default(mrrr_options* opt) {
   opt->engine_blocks_per_sm = 2;
   opt->width_scale = 1.0;
   opt->vector_precision = 1;
+  opt->singleton_rq = 1;
   return MRRR_OK;
 }
 
@@ -578,9 +580,8 @@ mrrr_status mrrr_plan_create(mrrr_plan** plan, const mrrr_options* opt) {
   }
   const int mw = o.multisection_width;
   if (mw < 0 || mw > 32 || (mw & (mw - 1)) != 0 || o.root_side < 0 || o.root_side > 2 ||
-      o.vector_precision < 0 || o.vector_precision > 2 || o.singleton_rq < 0 || o.singleton_rq > 4)
+      o.vector_precision < 0 || o.vector_precision > 2 || o.singleton_rq < -1 || o.singleton_rq > 4)
     return MRRR_ERR_ARG;
-  if (o.singleton_rq > 0 && o.vector_precision == 2) return MRRR_ERR_NOTIMPL;
   if (o.gap_tol >= 1.0 || o.classify_rtol >= 0.25 || o.threads_per_block % 32 != 0) return MRRR_ERR_ARG;
   int dev = 0, nsm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return MRRR_ERR_CUDA;

@@ -234,13 +234,9 @@ __global__ void k_root32_copy(Dev v, int64_t n_total) {
   }
 }
 
-// The division-free Sturm count of count_step() in FP32.
-__device__ __forceinline__ int negcount32(const float2* __restrict__ r, int m, float tau) {
-  const int pivexp = (__float_as_int(kPivmin32) >> 23) & 0xff;
-  float a = -tau, b = 1.0f;
-  int neg = 0;
-  for (int i = 0; i < m; ++i) {
-    const float2 x = r[i];
+// One row of the division-free Sturm count of count_step() in FP32.
+__device__ __forceinline__ void count_step32(float2 x, float tau, int pivexp, float& a, float& b, int& neg) {
+  {
     float c = fmaf(x.x, b, a);
     int ci = __float_as_int(c);
     const int bi = __float_as_int(b);
@@ -258,6 +254,29 @@ __device__ __forceinline__ int negcount32(const float2* __restrict__ r, int m, f
     const int aexp = (ai >> 23) & 0xff;
     a = (aexp - k <= 0) ? 0.0f : (aexp - k >= 255 ? __int_as_float((ai & 0x80000000) | 0x7f000000)
                                                    : __int_as_float(ai - (k << 23)));
+  }
+}
+
+// The FP32 count over m rows, kPrefetch rows loaded ahead into registers so
+// that the loads stay off the recurrence's critical path.
+__device__ __forceinline__ int negcount32(const float2* __restrict__ r, int m, float tau) {
+  const int pivexp = (__float_as_int(kPivmin32) >> 23) & 0xff;
+  float a = -tau, b = 1.0f;
+  int neg = 0;
+  float2 cur[kPrefetch], nxt[kPrefetch];
+#pragma unroll
+  for (int u = 0; u < kPrefetch; ++u) cur[u] = u < m ? __ldg(r + u) : make_float2(1.0f, 0.0f);
+  for (int i0 = 0; i0 < m; i0 += kPrefetch) {
+#pragma unroll
+    for (int u = 0; u < kPrefetch; ++u) {
+      const int i = i0 + kPrefetch + u;
+      nxt[u] = i < m ? __ldg(r + i) : make_float2(1.0f, 0.0f);
+    }
+#pragma unroll
+    for (int u = 0; u < kPrefetch; ++u)
+      if (i0 + u < m) count_step32(cur[u], tau, pivexp, a, b, neg);
+#pragma unroll
+    for (int u = 0; u < kPrefetch; ++u) cur[u] = nxt[u];
   }
   return neg;
 }
@@ -479,11 +498,20 @@ __global__ void __launch_bounds__(kEngThreads, kEngCtasPerSm) k_engine(Dev v) {
   const long long nshort = min(v.ctl->nlist2, (long long)v.max_list - nlong);
   const long long lanes_total = (long long)((double)v.nsm * 4 * 32 * v.width_scale);
   // chunks: the long intervals first, then the short ones, each part with
-  // the width its own length allows; a chunk is one warp's 32 / T intervals
+  // the width its own length allows; a chunk is one warp's 32 / T intervals.
+  // Long intervals at width 1 are split into whole waves (every SM
+  // sub-partition gets the same number of full chunks) and a remainder that
+  // takes the width its own length allows: its few intervals then finish in
+  // fewer, wider passes on every sub-partition instead of a third (or later)
+  // full-length chunk on some of them.
   const int T_long = width_for(nlong, lanes_total, v.fixed_width);
+  const long long wave = (long long)v.nsm * 4 * 32;
+  const long long nmain = (T_long == 1 && v.fixed_width == 0) ? (nlong / wave) * wave : 0;
+  const int T_rest = width_for(nlong - nmain, lanes_total, v.fixed_width);
   const int T_short = width_for(nshort, lanes_total, v.fixed_width);
-  const long long g_long = 32 / T_long, g_short = 32 / T_short;
-  const long long nch_long = (nlong + g_long - 1) / g_long;
+  const long long g_rest = 32 / T_rest, g_short = 32 / T_short;
+  const long long nch_main = nmain / 32;
+  const long long nch_long = nch_main + (nlong - nmain + g_rest - 1) / g_rest;
   const long long nchunks = nch_long + (nshort + g_short - 1) / g_short;
   const long long total_warps = (long long)gridDim.x * (blockDim.x / 32);
   const long long rank = sched_rank(v);
@@ -499,10 +527,13 @@ __global__ void __launch_bounds__(kEngThreads, kEngCtasPerSm) k_engine(Dev v) {
     const long long chunk = sched_next(v, nchunks, total_warps, rank, first);
     if (chunk < 0) break;
     const bool is_long = chunk < nch_long;
-    const int T = is_long ? T_long : T_short;
+    const bool is_main = chunk < nch_main;
+    const int T = is_main ? 1 : is_long ? T_rest : T_short;
     const int pt = lane % T;
     const int groups = 32 / T, grp = lane / T;
-    const long long item = (is_long ? chunk : chunk - nch_long) * groups + grp;
+    const long long item = is_main   ? chunk * 32 + lane
+                           : is_long ? nmain + (chunk - nch_main) * groups + grp
+                                     : (chunk - nch_long) * groups + grp;
     const long long nlist = is_long ? nlong : nshort;
     Iv q{};
     bool have = false;

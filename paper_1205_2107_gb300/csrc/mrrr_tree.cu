@@ -216,9 +216,7 @@ __device__ double dstqds_child_pred(const double2* __restrict__ pdl, const doubl
   return growth;
 }
 
-constexpr int kShiftTries = 10;  // per side
-
-// Candidate shift t (0 .. 2 kShiftTries - 1) of a cluster: even t the left
+// Candidate shift t (0 .. 19: ten per side) of a cluster: even t the left
 // end lo_f - delta, odd t the right end hi_l + delta, delta = 4 eps |end| 4^(t/2)
 // (+ 4 pivmin).
 __device__ __forceinline__ double child_shift(int t, double lo_f, double hi_l, double pivmin) {
@@ -344,6 +342,7 @@ __global__ void k_childrep_first(Dev v) {
       c.rep = base;
       c.pad_ = 1;
       c.sigma_rel = gd0;  // growth of the first candidate, for the second wave
+      c.pivmin = R;       // and its largest entry (candidate 0's rows stay at base)
       v.node[id] = c;
       diag(v.ctl, DIAG_CHILD_WAVE2);
       continue;
@@ -362,11 +361,13 @@ __global__ void k_childrep_first(Dev v) {
 
 // Phase 2, for nodes whose first candidate failed: a group of 8 lanes per
 // node (4 nodes per warp) evaluates 8 further candidates spread over the
-// ladder of child_shift (growth only); the first candidate in ladder order
-// whose growth max|D+| is at most 8 spdiam is taken, else the one with the
-// smallest growth among these and the first candidate (counted in the
-// diagnostics).  The chosen transform is then recomputed with stores into
-// the rows reserved in phase 1.
+// ladder of child_shift; the first candidate in ladder order whose growth
+// max|D+| is at most 8 spdiam is taken, else the one with the smallest
+// growth among these and the first candidate (counted in the diagnostics).
+// When the pool has room every candidate stores into rows of its own and
+// the winner's rows become the child, in one pass; otherwise the pass
+// measures growth only and the chosen transform is computed again with
+// stores into the rows reserved in phase 1 (which hold candidate 0's).
 constexpr int kPhase2Group = 8;
 __constant__ int kPhase2Cands[kPhase2Group] = {1, 2, 3, 4, 8, 9, 18, 19};
 
@@ -386,15 +387,28 @@ __global__ void k_childrep(Dev v) {
       c = v.node[id];
       mine = c.pad_ == 1;
     }
-    double g = INFINITY, sigma = 0.0;
+    double g = INFINITY, sigma = 0.0, Rc = 0.0;
     int cand = 0;
     Node p{};
+    int64_t base = -1;
+    if (mine && gl == 0) {
+      const int m = v.blk[c.block].m;
+      const int64_t rows = (int64_t)kPhase2Group * m;
+      if (v.ctl->pool_top + rows <= v.pool_cap / 2) {
+        base = (int64_t)atomicAdd((unsigned long long*)&v.ctl->pool_top, (unsigned long long)rows);
+        atomicMax((unsigned long long*)&v.ctl->pool_need, (unsigned long long)(base + rows));
+        if (base + rows > v.pool_cap) base = -1;
+      }
+    }
+    base = __shfl_sync(0xffffffffu, base, leader);
     if (mine) {
       p = v.node[c.parent];
       const int m = v.blk[c.block].m;
       cand = kPhase2Cands[gl];
       sigma = child_shift(cand, v.lo[c.first], v.hi[c.last], p.pivmin);
-      g = dstqds_child<false>(v.rep_dl + p.rep, v.rep_ul + p.rep, nullptr, nullptr, m, sigma, p.pivmin);
+      const int64_t at = base >= 0 ? base + (int64_t)gl * m : 0;
+      Rc = dstqds_child_pred(v.rep_dl + p.rep, v.rep_ul + p.rep, v.rep_dl + at, v.rep_ul + at, m, sigma, p.pivmin,
+                             base >= 0, &g);
     }
     const unsigned gbits = 0xffu << leader;
     const bool ok = mine && g <= 8.0 * c.spdiam;
@@ -407,20 +421,33 @@ __global__ void k_childrep(Dev v) {
       const int oc = __shfl_xor_sync(0xffffffffu, bc, o);
       if (og < bg || (og == bg && oc < bc)) bg = og, bc = oc;
     }
-    if (!mine || gl != 0) continue;
-    const int m = v.blk[c.block].m;
-    int pick;
+    // the lane (within the group) of the pick, -1 for candidate 0
+    int pl;
     if (okmask) {
-      pick = kPhase2Cands[__ffs(okmask) - 1 - leader];
+      pl = __ffs(okmask) - 1 - leader;
     } else {
       // the first candidate's growth was kept in sigma_rel by phase 1
-      pick = c.sigma_rel <= bg ? 0 : bc;
-      diag(v.ctl, DIAG_CHILD_GROWTH);
+      const int pick = c.sigma_rel <= bg ? 0 : bc;
+      pl = -1;
+      for (int k = 0; k < kPhase2Group; ++k)
+        if (kPhase2Cands[k] == pick) pl = k;
     }
+    const double R_pick = __shfl_sync(0xffffffffu, Rc, leader + max(pl, 0));
+    if (!mine || gl != 0) continue;
+    if (!okmask) diag(v.ctl, DIAG_CHILD_GROWTH);
+    const int m = v.blk[c.block].m;
+    const int pick = pl < 0 ? 0 : kPhase2Cands[pl];
     const double sig = child_shift(pick, v.lo[c.first], v.hi[c.last], p.pivmin);
-    const double R =
-        dstqds_child<true>(v.rep_dl + p.rep, v.rep_ul + p.rep, v.rep_dl + c.rep, v.rep_ul + c.rep, m, sig, p.pivmin);
-    set_child(v, id, c, p, c.rep, sig, R);
+    if (pl < 0) {  // candidate 0: its rows and largest entry from phase 1
+      set_child(v, id, c, p, c.rep, sig, c.pivmin);
+    } else if (base >= 0) {
+      set_child(v, id, c, p, base + (int64_t)pl * m, sig, R_pick);
+    } else {
+      const double R = dstqds_child<true>(v.rep_dl + p.rep, v.rep_ul + p.rep, v.rep_dl + c.rep, v.rep_ul + c.rep, m,
+                                          sig, p.pivmin);
+      set_child(v, id, c, p, c.rep, sig, R);
+      diag(v.ctl, DIAG_CHILD_RESTORE);
+    }
   }
 }
 

@@ -632,15 +632,25 @@ __global__ void __launch_bounds__(kFixThreads) k_orth_fix(Dev v) {
 // in any problem, eigenvalues equal to the last bit that were finished on
 // different nodes (sigma_abs + local value, each rounded) can come out one or
 // two ulps out of order.  One CTA per problem: a sweep over all of W finds
-// whether any neighbours are out of order (the usual answer is no); if so,
-// odd-even transposition passes with every thread on its own pairs swap the
-// values and queue the swapped pairs, whose columns of Z the warps then swap;
-// the passes stop after two without a swap.
+// whether any neighbours are out of order (the usual answer is no).  If so,
+// and the running maximum of W exceeds no entry by more than kTieUlps ulps,
+// the entries are rounding ties: each takes the running maximum (it moves by
+// at most those few ulps, its column stays).  Otherwise odd-even
+// transposition passes with every thread on its own pairs swap the values
+// and queue the swapped pairs, whose columns of Z the warps then swap; the
+// passes stop after two without a swap.
 constexpr int kSwapQueue = 512;
+constexpr double kTieUlps = 16.0;
+
+__device__ __forceinline__ bool is_tie(double run, double w) {
+  const double def = run - w;
+  return !isnan(w) && (def <= kTieUlps * kEps * fmax(fabs(run), fabs(w)) || def <= 1e-300);
+}
 
 __global__ void __launch_bounds__(kFixThreads) k_fix_order(Dev v) {
   __shared__ int nq;
   __shared__ int64_t queue[kSwapQueue];
+  __shared__ double cmax[kFixThreads];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   constexpr int nw = kFixThreads / 32;
   for (int64_t p = blockIdx.x; p < v.batch; p += gridDim.x) {
@@ -650,6 +660,31 @@ __global__ void __launch_bounds__(kFixThreads) k_fix_order(Dev v) {
     int bad = 0;
     for (int64_t i = threadIdx.x; i + 1 < q.k; i += kFixThreads) bad |= W[i] > W[i + 1];
     if (!__syncthreads_or(bad)) continue;
+    // rounding ties only?  Thread t takes a contiguous chunk; the running
+    // maximum enters it as the maximum of the chunks before.
+    const int64_t per = (q.k + kFixThreads - 1) / kFixThreads;
+    const int64_t a = min((int64_t)threadIdx.x * per, (int64_t)q.k), b = min(a + per, (int64_t)q.k);
+    double m = -INFINITY;
+    for (int64_t i = a; i < b; ++i) m = fmax(m, W[i]);
+    cmax[threadIdx.x] = m;
+    __syncthreads();
+    double run = -INFINITY;
+    for (int t = 0; t < (int)threadIdx.x; ++t) run = fmax(run, cmax[t]);
+    const double run0 = run;
+    int ties = 1;
+    for (int64_t i = a; i < b; ++i) {
+      run = fmax(run, W[i]);
+      ties &= is_tie(run, W[i]);
+    }
+    if (__syncthreads_and(ties)) {
+      run = run0;
+      for (int64_t i = a; i < b; ++i) {
+        run = fmax(run, W[i]);
+        W[i] = run;
+      }
+      __syncthreads();
+      continue;
+    }
     int quiet = 0;
     for (int pass = 0; pass < 2 * q.k + 2 && quiet < 2; ++pass) {
       int swapped = 0;

@@ -44,6 +44,7 @@ def test_options_defaults(lib):
     assert o.gap_tol == 1e-4  # floor; blocks of order m use max(gap_tol, 1/m)
     assert o.classify_rtol == 2.0 ** -20
     assert o.max_depth == 64 and o.threads_per_block % 32 == 0
+    assert o.singleton_rq == 1 and o.vector_precision == 1
     assert lib.mrrr_options_default(None) == _lib.ERR_ARG
 
 

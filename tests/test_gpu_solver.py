@@ -222,9 +222,10 @@ RQ_CASES = {
 }
 
 
-@pytest.mark.parametrize("steps", [1, 2])
+@pytest.mark.parametrize("steps", [-1, 1, 2])
 @pytest.mark.parametrize("case", sorted(RQ_CASES))
 def test_singleton_rayleigh_quotient_correction(case, steps):
+    """-1: full bisection, no correction; 1 (the default), 2: corrections."""
     d, e = RQ_CASES[case]()
     plan = api.Plan(singleton_rq=steps)
     assert_parity(d, e, plan=plan)
@@ -237,7 +238,7 @@ def test_singleton_rayleigh_quotient_correction(case, steps):
 def test_singleton_rq_takes_one_more_factorization_per_step():
     d, e = inputs.uniform(400, 5)
     counts = []
-    for steps in (0, 1, 2):
+    for steps in (-1, 1, 2):
         plan = api.Plan(singleton_rq=steps)
         solve(d, e, plan=plan)
         counts.append(plan.info()["twisted_solves"])
@@ -248,4 +249,9 @@ def test_singleton_rq_options_are_checked():
     with pytest.raises(_lib.MrrrError):
         api.Plan(singleton_rq=5)
     with pytest.raises(_lib.MrrrError):
-        api.Plan(singleton_rq=1, vector_precision=2)
+        api.Plan(singleton_rq=-2)
+    # double-double vectors make their own correction: the FP64 option is ignored
+    d, e = inputs.uniform(300, 6)
+    plan = api.Plan(singleton_rq=2, vector_precision=2)
+    assert_parity(d, e, plan=plan)
+    assert plan.info()["twisted_solves"] == 2 * 300
