@@ -93,6 +93,11 @@ typedef struct mrrr_options {
                               at most m/8 for a block of order m; negative = none) */
   double width_scale;      /* scales the resident lanes when the engine chooses its
                               multisection width (1.0; larger = more points per interval) */
+  double prebisect_rtol;   /* relative width to which root intervals are first bisected
+                              on an FP32 copy of the root rows (2^-17); FP64 then confirms
+                              each bracket, widened by 4x this relative, before bisecting
+                              to classify_rtol.  Smaller moves halvings from the FP64 pipe
+                              to the FP32 one (at most 2^-20; never below classify_rtol) */
   int multisection_width;  /* 0: the engine picks the points per interval from the length of
                               its work list, and consecutive eigenvalues of one node whose
                               brackets coincide pool their points (default); 1..32 (a power
@@ -121,7 +126,9 @@ typedef struct mrrr_options {
                               lambda its Rayleigh quotient.  -1: no correction, every
                               singleton bisected to full relative accuracy (2 eps) and one
                               twisted factorization.  Ignored with vector_precision 2
-                              (which bisects fully and corrects in double-double) */
+                              (which bisects fully and corrects in double-double) and by
+                              mrrr_stein_slice (full bisection: a slice's vector stage is
+                              bound by the latency of each factorization) */
   int reserved_[4];        /* zero */
 } mrrr_options;
 
@@ -258,10 +265,14 @@ mrrr_status mrrr_stein_batched(mrrr_plan* plan, int batch, const int64_t* d_off,
 /*
  * mrrr_autotune_batched: choose the launch shape of the batched solver for
  * one batch layout by timing it.  Not in the paper (a scheduling aid for
- * the batched pattern).  Candidates: engine_blocks_per_sm in {2, 1} x
- * width_scale (points per interval of the multisection) in {1, 0.5, 2};
- * each solves the batch once (after one untimed warm-up solve) with CUDA
- * events on stream.  The fastest becomes the plan's setting (the plan's
+ * the batched pattern).  Candidates: block shape (engine_blocks_per_sm in
+ * {2, 1}) x threads per interval (width_scale, which scales the multisection
+ * width and with it the bisection steps per pass, in {1, 0.5, 2}) x
+ * bisection steps before the vectors (singleton_rq in {1, -1}: singletons to
+ * 2^-36 then one Rayleigh-quotient correction, or to full accuracy; only the
+ * plan's own setting with vector_precision 2): 12 candidates, each solving
+ * the batch once (after one untimed warm-up solve) with CUDA events on
+ * stream.  The fastest becomes the plan's setting (the plan's
  * CUDA graph, if any, is rebuilt on the next call).  Arguments as in
  * mrrr_stein_batched; on return W and Z hold a valid solution.  The call
  * synchronises the stream.  Device-side errors are returned.
@@ -272,6 +283,8 @@ typedef struct mrrr_tuning {
   double width_scale;        /* chosen */
   double best_ms;            /* time of the chosen candidate */
   double default_ms;         /* time of the first candidate (the defaults) */
+  int singleton_rq;          /* chosen */
+  int pad_;
 } mrrr_tuning;
 
 mrrr_status mrrr_autotune_batched(mrrr_plan* plan, int batch, const int64_t* d_off, const double* d,

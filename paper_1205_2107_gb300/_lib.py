@@ -36,7 +36,7 @@ class Options(ctypes.Structure):
                 ("max_bisect_steps", c_int), ("engine_blocks_per_sm", c_int), ("threads_per_block", c_int),
                 ("vec_blocks_per_sm", c_int), ("use_graph", c_int), ("max_nodes", c_int64),
                 ("pool_rows", c_int64), ("cluster_rtol", c_double), ("root_perturb", c_double),
-                ("width_scale", c_double), ("multisection_width", c_int), ("root_side", c_int),
+                ("width_scale", c_double), ("prebisect_rtol", c_double), ("multisection_width", c_int), ("root_side", c_int),
                 ("vector_precision", c_int), ("singleton_rq", c_int),
                 ("reserved_", c_int * 4)]
 
@@ -56,7 +56,7 @@ class Info(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("engine_blocks_per_sm", c_int), ("configs", c_int), ("width_scale", c_double),
-                ("best_ms", c_double), ("default_ms", c_double)]
+                ("best_ms", c_double), ("default_ms", c_double), ("singleton_rq", c_int), ("pad_", c_int)]
 
 
 class Profile(ctypes.Structure):

@@ -392,8 +392,8 @@ def autotune_batched(d: torch.Tensor, e: torch.Tensor, layout: BatchLayout, *, p
     the candidates (mrrr_autotune_batched); the choice stays on the plan.
 
     One checked solve runs first so that the plan's capacities fit the
-    batch.  Returns the chosen engine_blocks_per_sm and width_scale with the
-    best and default times (ms).
+    batch.  Returns the chosen engine_blocks_per_sm, width_scale and
+    singleton_rq with the best and default times (ms).
     """
     d = _check_input(d, "d")
     e = _check_input(e, "e")
@@ -409,9 +409,11 @@ def autotune_batched(d: torch.Tensor, e: torch.Tensor, layout: BatchLayout, *, p
         _ptr(W), _ptr(layout.w_offsets), _ptr(Z), _ptr(layout.z_offsets), layout.n_total, layout.k_total,
         layout.n_max, _ptr(ws), nbytes, _stream_handle(d.device), ctypes.byref(t))
     _lib.check(rc, "mrrr_autotune_batched")
-    plan.options.update(engine_blocks_per_sm=int(t.engine_blocks_per_sm), width_scale=float(t.width_scale))
+    plan.options.update(engine_blocks_per_sm=int(t.engine_blocks_per_sm), width_scale=float(t.width_scale),
+                        singleton_rq=int(t.singleton_rq))
     return {"engine_blocks_per_sm": int(t.engine_blocks_per_sm), "width_scale": float(t.width_scale),
-            "best_ms": float(t.best_ms), "default_ms": float(t.default_ms), "configs": int(t.configs)}
+            "singleton_rq": int(t.singleton_rq), "best_ms": float(t.best_ms), "default_ms": float(t.default_ms),
+            "configs": int(t.configs)}
 
 
 PEAK_KINDS = {"dfma": 0, "dmma": 1, "ddiv": 2, "ffma": 3, "dfma_one_lane": 4, "dfma_latency": 5,

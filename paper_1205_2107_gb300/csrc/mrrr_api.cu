@@ -292,6 +292,7 @@ Dev make_dev(const mrrr_plan* p, const Layout& L, void* ws, int batch, const dou
   v.vec_dd = o.vector_precision == 2;
   // double-double vectors take their own correction from a fully bisected value
   v.rq_steps = o.vector_precision == 2 || o.singleton_rq < 0 ? 0 : o.singleton_rq;
+  v.root32_rtol = std::max(o.prebisect_rtol, o.classify_rtol);
   return v;
 }
 
@@ -312,11 +313,15 @@ mrrr_status cuda_status(cudaError_t e) { return e == cudaSuccess ? MRRR_OK : MRR
 // points, whose runs depend on the list), the root shift on the side the
 // whole range decides (root_side set by the entry point), and no neighbour
 // orthogonality safeguard (its runs depend on which columns the call holds).
+// Singletons are bisected to full accuracy, one factorization each: a
+// slice's vector stage holds few vectors per SM sub-partition and is bound
+// by the latency of each factorization, so a second one would not be hidden.
 void slice_overrides(const mrrr_plan* p, const ProblemArgs& a, Dev& v) {
   if (!a.slice) return;
   v.fixed_width = p->opt.multisection_width > 0 ? p->opt.multisection_width : kSliceWidth;
   v.root_side = a.slice;  // 1 left, 2 right (set by mrrr_stein_slice)
   v.no_orth_fix = 1;
+  v.rq_steps = 0;
 }
 
 // One solve enqueued on s.  device_levels: every level up to max_depth is
@@ -548,6 +553,7 @@ mrrr_status mrrr_options_default(mrrr_options* opt) {
   opt->root_perturb = 64.0;
   opt->engine_blocks_per_sm = 2;
   opt->width_scale = 1.0;
+  opt->prebisect_rtol = 0x1p-17;
   opt->vector_precision = 1;
   opt->singleton_rq = 1;
   return MRRR_OK;
@@ -573,6 +579,7 @@ mrrr_status mrrr_plan_create(mrrr_plan** plan, const mrrr_options* opt) {
     if (opt->use_graph > 0) o.use_graph = 1;
     if (opt->engine_blocks_per_sm > 0) o.engine_blocks_per_sm = std::min(opt->engine_blocks_per_sm, 2);
     if (opt->width_scale > 0) o.width_scale = opt->width_scale;
+    if (opt->prebisect_rtol > 0) o.prebisect_rtol = std::max(opt->prebisect_rtol, 0x1p-20);
     if (opt->multisection_width > 0) o.multisection_width = opt->multisection_width;
     if (opt->root_side > 0) o.root_side = opt->root_side;
     if (opt->vector_precision > 0) o.vector_precision = opt->vector_precision;
@@ -709,6 +716,9 @@ mrrr_status mrrr_autotune_batched(mrrr_plan* plan, int batch, const int64_t* d_o
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   static const int kCtas[] = {2, 1};
   static const double kWidth[] = {1.0, 0.5, 2.0};
+  // bisection steps before the vector stage: the default (singletons to
+  // 2^-36, one Rayleigh-quotient correction) or full bisection (2 eps)
+  static const int kRq[] = {1, -1};
   const mrrr_options saved = plan->opt;
   const bool timing = plan->timer.on;
   plan->timer.on = false;
@@ -725,10 +735,13 @@ mrrr_status mrrr_autotune_batched(mrrr_plan* plan, int batch, const int64_t* d_o
   // one untimed solve first: the timed candidates then all run warm
   plan->opt.use_graph = 0;
   st = solve(plan, a, d, e, W, Z, n_total, k_total, n_max, workspace, ws_bytes, s, true);
-  for (int ci = 0; ci < 2 && st == MRRR_OK; ++ci) {
-    for (int wi = 0; wi < 3 && st == MRRR_OK; ++wi) {
+  for (int k = 0; k < 12 && st == MRRR_OK; ++k) {
+    const int ci = k / 6, wi = (k / 2) % 3, ri = k % 2;
+    {
+      if (plan->opt.vector_precision == 2 && ri == 1) continue;  // the option does not apply
       plan->opt.engine_blocks_per_sm = kCtas[ci];
       plan->opt.width_scale = kWidth[wi];
+      plan->opt.singleton_rq = plan->opt.vector_precision == 2 ? saved.singleton_rq : kRq[ri];
       cudaEventRecord(e0, s);
       st = solve(plan, a, d, e, W, Z, n_total, k_total, n_max, workspace, ws_bytes, s, true);
       cudaEventRecord(e1, s);
@@ -746,6 +759,7 @@ mrrr_status mrrr_autotune_batched(mrrr_plan* plan, int batch, const int64_t* d_o
         best = ms;
         out->engine_blocks_per_sm = kCtas[ci];
         out->width_scale = kWidth[wi];
+        out->singleton_rq = plan->opt.singleton_rq;
       }
     }
   }
@@ -756,6 +770,7 @@ mrrr_status mrrr_autotune_batched(mrrr_plan* plan, int batch, const int64_t* d_o
   if (st != MRRR_OK) return st;
   plan->opt.engine_blocks_per_sm = out->engine_blocks_per_sm;
   plan->opt.width_scale = out->width_scale;
+  plan->opt.singleton_rq = out->singleton_rq;
   ++plan->opt_version;
   out->best_ms = best;
   out->configs = tried;

@@ -215,11 +215,10 @@ __global__ void k_list_write(Dev v) {
 // by a small relative amount.  The FP32 pipe issues about 60 times faster
 // than the FP64 pipe on this part, so the first halvings of every root
 // interval run on an FP32 copy of the rows, down to a relative width of
-// kRoot32Width.  FP64 then confirms the bracket, widened by kRoot32Margin
-// relative and grown until two FP64 counts hold it, before bisecting to the
-// classification accuracy.  No FP32 result is trusted without that check.
-constexpr float kRoot32Width = 0x1p-13f;
-constexpr double kRoot32Margin = 0x1p-11;
+// root32_rtol (option prebisect_rtol, 2^-17 by default).  FP64 then
+// confirms the bracket, widened by 4 root32_rtol relative and grown until
+// two FP64 counts hold it, before bisecting to the classification accuracy.
+// No FP32 result is trusted without that check.
 constexpr float kPivmin32 = 0x1p-60f;
 
 // FP32 rows of the root representations (D, LLD), in the eigenvector
@@ -281,31 +280,6 @@ __device__ __forceinline__ int negcount32(const float2* __restrict__ r, int m, f
   return neg;
 }
 
-// One thread per root interval of the list: FP32 bisection from the block's
-// Gershgorin bracket; the result goes to lo/hi for the FP64 check.
-__global__ void k_root32(Dev v) {
-  const long long nlist = min(v.ctl->nlist, (long long)v.max_list);
-  const float2* rows = root32_rows(v);
-  for (long long it = gtid(); it < nlist; it += gstride()) {
-    const int64_t w = v.ilist[it];
-    const Node nd = v.node[v.snode[w]];
-    const Block bk = v.blk[nd.block];
-    const int j = v.sj[w];
-    float lo = (float)bk.gl, hi = (float)bk.gu;
-    for (int step = 0; step < 48; ++step) {
-      if (hi - lo <= kRoot32Width * fmaxf(fabsf(lo), fabsf(hi))) break;
-      const float mid = 0.5f * (lo + hi);
-      if (!(mid > lo && mid < hi)) break;
-      if (negcount32(rows + bk.row0, bk.m, mid) >= j)
-        hi = mid;
-      else
-        lo = mid;
-    }
-    v.lo[w] = (double)lo;
-    v.hi[w] = (double)hi;
-  }
-}
-
 // Per-interval state, replicated in every lane of the interval's group.
 struct Iv {
   double lo, hi, plo, phi, delta, atol, pivmin;
@@ -334,7 +308,7 @@ __device__ __forceinline__ void iv_load(const Dev& v, int64_t w, Iv& q) {
     // further until they hold), inside the block's Gershgorin bracket
     q.plo = fmax(v.lo[w], bk.gl);
     q.phi = fmin(v.hi[w], bk.gu);
-    q.delta = kRoot32Margin * fmax(fabs(q.plo), fabs(q.phi)) + (q.phi - q.plo) + 4.0 * rn.pivmin;
+    q.delta = 4.0 * v.root32_rtol * fmax(fabs(q.plo), fabs(q.phi)) + (q.phi - q.plo) + 4.0 * rn.pivmin;
     q.lo = fmax(q.plo - q.delta, bk.gl);
     q.hi = fmin(q.phi + q.delta, bk.gu);
     q.phase = PH_VERIFY;
@@ -475,6 +449,78 @@ __device__ __forceinline__ int width_for(long long nlist, long long lanes_total,
   int T = 1;
   while (T < 32 && 2LL * T * nlist <= lanes_total) T *= 2;
   return T;
+}
+
+// FP32 bisection of the root intervals from their blocks' Gershgorin
+// brackets; the results go to lo/hi for the FP64 check.  Chunks spread over
+// the SM sub-partitions by the scheduler, cut like the engine's lists: whole
+// waves of chunks with one interval per lane, and a remainder whose few
+// intervals take T lanes each (T points per pass, the first point whose
+// count reaches j and the one before it bracket the eigenvalue).  With a
+// fixed schedule (slices, options) every interval takes one lane, so that
+// its bracket does not depend on the list it is in.
+constexpr int kRoot32CtasPerSm = 4;
+
+__global__ void __launch_bounds__(128) k_root32(Dev v) {
+  const int lane = threadIdx.x & 31;
+  const long long nlist = min(v.ctl->nlist, (long long)v.max_list);
+  const float2* rows = root32_rows(v);
+  const float width = (float)v.root32_rtol;
+  const long long wave = (long long)v.nsm * 4 * 32;
+  const bool fixed = v.fixed_width > 0;
+  const long long nmain = fixed ? nlist : (nlist / wave) * wave;
+  const int T_rest = fixed ? 1 : width_for(nlist - nmain, wave, 0);
+  const long long g_rest = 32 / T_rest;
+  const long long nch_main = (nmain + 31) / 32;
+  const long long nchunks = nch_main + (nlist - nmain + g_rest - 1) / g_rest;
+  const long long total_warps = (long long)gridDim.x * (blockDim.x / 32);
+  const long long rank = sched_rank(v);
+  bool first = true;
+  for (;;) {
+    const long long chunk = sched_next(v, nchunks, total_warps, rank, first);
+    if (chunk < 0) break;
+    const bool is_main = chunk < nch_main;
+    const int T = is_main ? 1 : T_rest;
+    const int pt = lane % T, lead = lane - pt;
+    const long long item = is_main ? chunk * 32 + lane : nmain + (chunk - nch_main) * g_rest + lane / T;
+    const bool mine = is_main ? item < nmain : item < nlist;
+    int64_t w = 0, row0 = 0;
+    int j = 0, m = 0;
+    float lo = 0.f, hi = 0.f;
+    if (mine) {
+      w = v.ilist[item];
+      const Block bk = v.blk[v.node[v.snode[w]].block];
+      j = v.sj[w];
+      m = bk.m;
+      row0 = bk.row0;
+      lo = (float)bk.gl;
+      hi = (float)bk.gu;
+    }
+    bool have = mine;
+    for (int step = 0; step < 48; ++step) {
+      if (have && hi - lo <= width * fmaxf(fabsf(lo), fabsf(hi))) have = false;
+      const float tau = lo + (hi - lo) * ((float)(pt + 1) / (float)(T + 1));
+      // the group stops when a point is not strictly inside its bracket
+      bool inside = !have || (tau > lo && tau < hi);
+      for (int o = 1; o < T; o <<= 1) inside &= __shfl_xor_sync(0xffffffffu, inside, o) != 0;
+      if (!inside) have = false;
+      if (!__any_sync(0xffffffffu, have)) break;
+      const int cnt = have ? negcount32(rows + row0, m, tau) : 0;
+      int kfirst = T;
+      for (int k = T - 1; k >= 0; --k)
+        if (__shfl_sync(0xffffffffu, cnt, lead + k) >= j) kfirst = k;
+      if (have) {
+        const float nlo = kfirst > 0 ? lo + (hi - lo) * ((float)kfirst / (float)(T + 1)) : lo;
+        const float nhi = kfirst < T ? lo + (hi - lo) * ((float)(kfirst + 1) / (float)(T + 1)) : hi;
+        lo = nlo;
+        hi = nhi;
+      }
+    }
+    if (mine && pt == 0) {
+      v.lo[w] = (double)lo;
+      v.hi[w] = (double)hi;
+    }
+  }
 }
 
 // Phase 0 drains the long intervals (front of the list), phase 1 the short
@@ -671,7 +717,9 @@ void launch_engine_mode(const Dev& v, const Grid& g, cudaStream_t s, int64_t n_t
   if (MODE == MODE_ROOT) {
     k_root32_copy<<<g.slot_blocks, 256, 0, s>>>(v, n_total);
     count_launch();
-    k_root32<<<g.slot_blocks, 128, 0, s>>>(v);
+    k_sched_reset<<<1, kSchedSlots, 0, s>>>(v);
+    count_launch();
+    k_root32<<<g.nsm * kRoot32CtasPerSm, 128, 0, s>>>(v);
     count_launch();
   }
   k_sched_reset<<<1, kSchedSlots, 0, s>>>(v);

@@ -114,6 +114,7 @@ struct Ctl {
   unsigned long long stage_ns[16];  // per-stage GPU time from device-clock marks (graph solves)
   unsigned long long t_last;        // global timer at the last mark
   long long orth_runs;              // runs of linked eigenvectors found by the safeguard
+  long long cand_top;               // rows of candidate child transforms in the scratch (per level)
 };
 
 // Indices of Ctl::diag (mirrored in mrrr_info.diag).
@@ -179,6 +180,7 @@ struct Dev {
   double rtol;          // root classification accuracy
   double rtol_cluster;  // accuracy of cluster eigenvalues (shift placement, children)
   double root_perturb;  // root perturbation size in ulps
+  double root32_rtol;   // relative width of the FP32 pre-bisection of root intervals
   int max_depth;
   int max_bisect;
   int engine_ctas;      // engine CTAs per SM (1 or 2)
@@ -346,6 +348,17 @@ __device__ __forceinline__ long long sched_next(const Dev& v, long long nchunks,
   }
   first = false;
   return __shfl_sync(0xffffffffu, c, 0);
+}
+
+// Candidate representation rows in the eigenvector scratch, which is idle
+// while the root representations and the tree are built: two planes of
+// double2 (the pool's layout), each half of the scratch.
+__device__ __forceinline__ int64_t cand_capacity(const Dev& v) {
+  return (int64_t)((size_t)v.vscr_threads * (size_t)v.vscr_rows * (v.vec_dd ? 4 : 2) / 4);
+}
+__device__ __forceinline__ double2* cand_dl(const Dev& v) { return reinterpret_cast<double2*>(v.vscr); }
+__device__ __forceinline__ double2* cand_ul(const Dev& v) {
+  return reinterpret_cast<double2*>(v.vscr) + cand_capacity(v);
 }
 
 __device__ __forceinline__ int64_t gtid() { return (int64_t)blockIdx.x * blockDim.x + threadIdx.x; }

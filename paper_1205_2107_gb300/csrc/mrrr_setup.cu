@@ -308,7 +308,10 @@ __device__ __forceinline__ double root_shift(int t, double gl, double gu, double
 // the ladder with stores while lanes 1..11 test the others; if the first
 // fails, the first that holds is factored again with stores.  The seeded
 // perturbation, the norm of the rows and the bracket counts also run across
-// the lanes, so the block costs one or two sequential passes over its rows.
+// the lanes.  When the eigenvector scratch has room for 11 rows per row of
+// T, lanes 1..11 store their factorizations there too and the warp copies a
+// winner other than lane 0's into place: the block then costs one
+// sequential pass over its rows; otherwise the winner is factored again.
 __global__ void k_root(Dev v) {
   const int nblocks = v.ctl->nblocks;
   const int lane = threadIdx.x & 31;
@@ -361,12 +364,28 @@ __global__ void k_root(Dev v) {
     // wanted range in the lower half, unless the side is fixed by the options
     const bool left = v.root_side == 1 ? true : v.root_side == 2 ? false : (bk.js + bk.je) <= (m + 1);
     bool ok_t = false;
-    if (lane < kRootTries) ok_t = root_factor(v, q, lr0, m, root_shift(lane, gl, gu, spdiam, left), left, lane == 0,
-                                              dl, ul);
+    // candidate rows of lanes 1..11 in the scratch, at 11 rows per row of T
+    const bool spare = (int64_t)(kRootTries - 1) * (bk.row0 + m) <= cand_capacity(v);
+    const int64_t srow = (int64_t)(kRootTries - 1) * bk.row0 + (int64_t)(lane - 1) * m;
+    if (lane < kRootTries) {
+      const bool own = lane == 0;
+      ok_t = root_factor(v, q, lr0, m, root_shift(lane, gl, gu, spdiam, left), left, own || spare,
+                         own ? dl : cand_dl(v) + srow, own ? ul : cand_ul(v) + srow);
+    }
     const unsigned okm = __ballot_sync(0xffffffffu, ok_t);
     const int t = okm ? __ffs(okm) - 1 : kRootTries - 1;
     const double sigma = root_shift(t, gl, gu, spdiam, left);
-    if (t > 0 && lane == 0) root_factor(v, q, lr0, m, sigma, left, true, dl, ul);
+    if (okm && t > 0 && spare) {  // the winner's rows from the scratch
+      __syncwarp();
+      const int64_t from = (int64_t)(kRootTries - 1) * bk.row0 + (int64_t)(t - 1) * m;
+      for (int i = lane; i < m; i += 32) {
+        dl[i] = cand_dl(v)[from + i];
+        ul[i] = cand_ul(v)[from + i];
+      }
+      __syncwarp();
+    } else if (t > 0 && lane == 0) {
+      root_factor(v, q, lr0, m, sigma, left, true, dl, ul);
+    }
     if (!okm && lane == 0) {
       set_status(v.ctl, MRRR_ERR_NOCONV);
       diag(v.ctl, DIAG_ROOT_SHIFT);

@@ -18,6 +18,7 @@ __global__ void k_level_start(Dev v) {
   if (threadIdx.x == 0 && blockIdx.x == 0 && !v.ctl->done) {
     v.ctl->level_begin = v.ctl->nodes;
     v.ctl->level_new = 0;
+    v.ctl->cand_top = 0;
   }
 }
 
@@ -246,10 +247,13 @@ __device__ __forceinline__ void set_child(Dev& v, int64_t id, Node c, const Node
 // is a sequential recurrence, so a level with few clusters is bound by the
 // latency of one pass: trying every candidate at once replaces up to three
 // passes (first candidate, the others, the winner again with stores) by one.
-// Candidate 0 is always computed with stores; when the pool has room, every
-// candidate of the group stores into rows of its own and the winner's rows
-// become the child (the others stay unused in the pool); otherwise a winner
-// other than candidate 0 is computed once more with stores.  A node whose
+// Candidate 0 always stores into the node's rows of the pool.  When the pool
+// has room, every other candidate of the group stores into rows of its own
+// there and the winner's rows become the child (the others stay unused);
+// else, when the eigenvector scratch (idle while the tree is built) has
+// room, the other candidates store there and the warp copies a winner's
+// rows into the node's rows; otherwise a winner other than candidate 0 is
+// computed once more with stores.  A node whose
 // evaluated candidates all fail before the whole ladder was tried goes to
 // the second wave (k_childrep).  Nodes whose rows do not fit take the
 // fallback (their vectors at the parent).  The choice is the same whatever
@@ -294,7 +298,7 @@ __global__ void k_childrep_first(Dev v) {
     Node c{};
     Node p{};
     int m = 0;
-    int64_t base = -1;
+    int64_t base = -1, sbase = -1;
     bool multi = false;
     if (mine) {
       c = v.node[id];
@@ -307,21 +311,32 @@ __global__ void k_childrep_first(Dev v) {
         base = (int64_t)atomicAdd((unsigned long long*)&v.ctl->pool_top, (unsigned long long)rows);
         atomicMax((unsigned long long*)&v.ctl->pool_need, (unsigned long long)(base + rows));
         if (base + rows > v.pool_cap) base = -1;
+        if (!multi && ncand > 1 && base >= 0) {  // candidates 1.. in the scratch
+          const int64_t srows = (int64_t)(ncand - 1) * m;
+          const int64_t at = (int64_t)atomicAdd((unsigned long long*)&v.ctl->cand_top, (unsigned long long)srows);
+          if (at + srows <= cand_capacity(v)) sbase = at;
+        }
       }
     }
     base = __shfl_sync(0xffffffffu, base, leader);
+    sbase = __shfl_sync(0xffffffffu, sbase, leader);
     multi = __shfl_sync(0xffffffffu, (int)multi, leader) != 0;
     const bool live = mine && base >= 0;
     if (mine && base < 0 && gl == 0) child_fallback(v, id, c);
     const bool cand = live && gl < ncand;
     const int t = cand ? kLadderCands[gl] : 0;
     double sigma = 0.0, gd = INFINITY, R = 0.0;
-    const bool stored = cand && (multi || gl == 0);
+    const bool scratch = !multi && sbase >= 0 && gl > 0;
+    const bool stored = cand && (multi || gl == 0 || scratch);
     if (cand) {
       sigma = child_shift(t, v.lo[c.first], v.hi[c.last], p.pivmin);
-      const int64_t at = base + (multi ? (int64_t)gl * m : 0);
-      R = dstqds_child_pred(v.rep_dl + p.rep, v.rep_ul + p.rep, v.rep_dl + at, v.rep_ul + at, m, sigma, p.pivmin,
-                            stored, &gd);
+      double2* odl = v.rep_dl + base + (multi ? (int64_t)gl * m : 0);
+      double2* oul = v.rep_ul + base + (multi ? (int64_t)gl * m : 0);
+      if (scratch) {
+        odl = cand_dl(v) + sbase + (int64_t)(gl - 1) * m;
+        oul = cand_ul(v) + sbase + (int64_t)(gl - 1) * m;
+      }
+      R = dstqds_child_pred(v.rep_dl + p.rep, v.rep_ul + p.rep, odl, oul, m, sigma, p.pivmin, stored, &gd);
     }
     const bool ok = cand && gd <= 8.0 * c.spdiam;
     const unsigned okmask = __ballot_sync(0xffffffffu, ok) & gbits;
@@ -337,6 +352,28 @@ __global__ void k_childrep_first(Dev v) {
     const double gd0 = __shfl_sync(0xffffffffu, gd, leader);
     const double sig_w = __shfl_sync(0xffffffffu, sigma, leader + max(win, 0));
     const double R_w = __shfl_sync(0xffffffffu, R, leader + max(win, 0));
+    // winners stored in the scratch: the whole warp copies their rows into
+    // the node's rows of the pool, one group after the other
+    {
+      const bool cp = live && gl == 0 && !multi && sbase >= 0 && win > 0;
+      __syncwarp();  // the candidates' stores are visible to the whole warp
+      unsigned todo = __ballot_sync(0xffffffffu, cp);
+      while (todo) {
+        const int src = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const int64_t dst = __shfl_sync(0xffffffffu, base, src);
+        const int mm = __shfl_sync(0xffffffffu, m, src);
+        const int64_t from = __shfl_sync(0xffffffffu, sbase, src) +
+                             (int64_t)(__shfl_sync(0xffffffffu, win, src) - 1) * mm;
+        const double2* sdl = cand_dl(v) + from;
+        const double2* sul = cand_ul(v) + from;
+        for (int i = lane; i < mm; i += 32) {
+          v.rep_dl[dst + i] = sdl[i];
+          v.rep_ul[dst + i] = sul[i];
+        }
+      }
+      __syncwarp();
+    }
     if (!live || gl != 0) continue;
     if (win < 0) {  // second wave: the rest of the ladder
       c.rep = base;
@@ -348,7 +385,7 @@ __global__ void k_childrep_first(Dev v) {
       continue;
     }
     if (!okmask) diag(v.ctl, DIAG_CHILD_GROWTH);
-    if (multi || win == 0) {
+    if (multi || win == 0 || sbase >= 0) {
       set_child(v, id, c, p, base + (multi ? (int64_t)win * m : 0), sig_w, R_w);
     } else {
       const double Rr = dstqds_child<true>(v.rep_dl + p.rep, v.rep_ul + p.rep, v.rep_dl + base, v.rep_ul + base, m,

