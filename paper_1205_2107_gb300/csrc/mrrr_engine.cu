@@ -523,6 +523,108 @@ __global__ void __launch_bounds__(128) k_root32(Dev v) {
   }
 }
 
+// How one engine launch cuts its list into chunks (one warp's intervals
+// each): the long intervals first, then the short ones, each part with the
+// width its own length allows.  Long intervals at width 1 are split into
+// whole waves (every SM sub-partition gets the same number of full chunks)
+// and a remainder that takes the width its own length allows: its few
+// intervals then finish in fewer, wider passes on every sub-partition
+// instead of a third (or later) full-length chunk on some of them.
+struct ChunkPlan {
+  long long nlong, nshort, nmain, nch_main, nch_long, nchunks;
+  int T_rest, T_short;
+};
+
+__device__ __forceinline__ ChunkPlan chunk_plan(const Dev& v) {
+  ChunkPlan c;
+  c.nlong = min(v.ctl->nlist, (long long)v.max_list);
+  c.nshort = min(v.ctl->nlist2, (long long)v.max_list - c.nlong);
+  const long long lanes_total = (long long)((double)v.nsm * 4 * 32 * v.width_scale);
+  const int T_long = width_for(c.nlong, lanes_total, v.fixed_width);
+  const long long wave = (long long)v.nsm * 4 * 32;
+  c.nmain = (T_long == 1 && v.fixed_width == 0) ? (c.nlong / wave) * wave : 0;
+  c.T_rest = width_for(c.nlong - c.nmain, lanes_total, v.fixed_width);
+  c.T_short = width_for(c.nshort, lanes_total, v.fixed_width);
+  const long long g_rest = 32 / c.T_rest, g_short = 32 / c.T_short;
+  c.nch_main = c.nmain / 32;
+  c.nch_long = c.nch_main + (c.nlong - c.nmain + g_rest - 1) / g_rest;
+  c.nchunks = c.nch_long + (c.nshort + g_short - 1) / g_short;
+  return c;
+}
+
+// The order of the main chunks, in the second half of the list's window
+// offsets (free once the list is written); the first half holds each
+// chunk's estimate while the order is built.
+__device__ __forceinline__ int64_t* chunk_perm(const Dev& v) { return v.lwin + (v.max_slots + 31) / 32; }
+
+// Halvings an interval still needs in this mode (0..63), from its bracket.
+template <int MODE>
+__device__ __forceinline__ int halvings_left(const Dev& v, int64_t w) {
+  double lo = v.lo[w], hi = v.hi[w];
+  if (MODE == MODE_REFINE) {
+    const double sig = v.node[v.snode[w]].sigma_rel;
+    lo -= sig;
+    hi -= sig;
+  }
+  const double goal = mode_rtol<MODE>(v) * fmax(fabs(lo), fabs(hi));
+  const double wdt = hi - lo;
+  if (!(wdt > goal) || !(goal > 0.0)) return 0;
+  return max(0, min(63, ilogb(wdt) - ilogb(goal) + 1));
+}
+
+// Cluster modes only (whose chunks' lengths vary with the gaps inside
+// their clusters): one CTA sorts the main chunks, four consecutive ones at a
+// time (one SM's share of a wave, so that an SM's warps keep reading
+// neighbouring representation rows), by the most halvings any of their
+// intervals needs, longest first, and deals these quads to the SMs in a
+// snake (wave 0 left to right, wave 1 right to left, ...), so that every SM
+// pairs long work with short.  The engine's scheduler hands chunk position
+// r to the warp of rank r, which sits on sub-partition r mod 4 of SM
+// (r mod (4 x SMs)) / 4.  Only the placement of chunks changes: each
+// chunk's intervals, and so the results, stay the same.
+constexpr int kOrderThreads = 1024;
+
+template <int MODE>
+__host__ __device__ constexpr bool ordered_mode() {
+  return MODE == MODE_PREREFINE || MODE == MODE_REFINE;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kOrderThreads) k_chunk_order(Dev v) {
+  if (v.ctl->done) return;
+  __shared__ unsigned long long hist[64];
+  const ChunkPlan cp = chunk_plan(v);
+  const long long nquad = cp.nch_main / 4;
+  if (nquad <= 0) return;
+  int64_t* est = v.lwin;
+  int64_t* perm = chunk_perm(v);
+  if (threadIdx.x < 64) hist[threadIdx.x] = 0;
+  __syncthreads();
+  for (long long qd = threadIdx.x; qd < nquad; qd += kOrderThreads) {
+    int e = 0;
+    for (int i = 0; i < 128; ++i) e = max(e, halvings_left<MODE>(v, v.ilist[qd * 128 + i]));
+    est[qd] = e;
+    atomicAdd(&hist[e], 1ull);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {  // start of each bucket, the largest first
+    unsigned long long at = 0;
+    for (int b = 63; b >= 0; --b) {
+      const unsigned long long n = hist[b];
+      hist[b] = at;
+      at += n;
+    }
+  }
+  __syncthreads();
+  const long long nsm = v.nsm;
+  for (long long qd = threadIdx.x; qd < nquad; qd += kOrderThreads) {
+    const long long k = (long long)atomicAdd(&hist[est[qd]], 1ull);
+    const long long wv = k / nsm, i = k % nsm;
+    const long long sm = (wv & 1) ? nsm - 1 - i : i;
+    for (int j = 0; j < 4; ++j) perm[wv * 4 * nsm + 4 * sm + j] = 4 * qd + j;
+  }
+}
+
 // Phase 0 drains the long intervals (front of the list), phase 1 the short
 // ones (back of the list), each with the width that its own length allows;
 // a warp moves on to phase 1 as soon as the long list is exhausted for it.
@@ -540,25 +642,11 @@ template <int MODE>
 __global__ void __launch_bounds__(kEngThreads, kEngCtasPerSm) k_engine(Dev v) {
   if ((MODE == MODE_PREREFINE || MODE == MODE_REFINE) && v.ctl->done) return;
   const int lane = threadIdx.x & 31;
-  const long long nlong = min(v.ctl->nlist, (long long)v.max_list);
-  const long long nshort = min(v.ctl->nlist2, (long long)v.max_list - nlong);
-  const long long lanes_total = (long long)((double)v.nsm * 4 * 32 * v.width_scale);
-  // chunks: the long intervals first, then the short ones, each part with
-  // the width its own length allows; a chunk is one warp's 32 / T intervals.
-  // Long intervals at width 1 are split into whole waves (every SM
-  // sub-partition gets the same number of full chunks) and a remainder that
-  // takes the width its own length allows: its few intervals then finish in
-  // fewer, wider passes on every sub-partition instead of a third (or later)
-  // full-length chunk on some of them.
-  const int T_long = width_for(nlong, lanes_total, v.fixed_width);
-  const long long wave = (long long)v.nsm * 4 * 32;
-  const long long nmain = (T_long == 1 && v.fixed_width == 0) ? (nlong / wave) * wave : 0;
-  const int T_rest = width_for(nlong - nmain, lanes_total, v.fixed_width);
-  const int T_short = width_for(nshort, lanes_total, v.fixed_width);
-  const long long g_rest = 32 / T_rest, g_short = 32 / T_short;
-  const long long nch_main = nmain / 32;
-  const long long nch_long = nch_main + (nlong - nmain + g_rest - 1) / g_rest;
-  const long long nchunks = nch_long + (nshort + g_short - 1) / g_short;
+  const ChunkPlan cp = chunk_plan(v);
+  const long long nlong = cp.nlong, nshort = cp.nshort, nmain = cp.nmain;
+  const long long nch_main = cp.nch_main, nch_long = cp.nch_long, nchunks = cp.nchunks;
+  const int T_rest = cp.T_rest, T_short = cp.T_short;
+  const int64_t* perm = chunk_perm(v);
   const long long total_warps = (long long)gridDim.x * (blockDim.x / 32);
   const long long rank = sched_rank(v);
   const double rtol = mode_rtol<MODE>(v);
@@ -570,8 +658,11 @@ __global__ void __launch_bounds__(kEngThreads, kEngCtasPerSm) k_engine(Dev v) {
   for (;;) {
     // the warp's next chunk (consecutive list entries: neighbouring slots, so
     // the same node or problem: the lanes share row lengths and often rows)
-    const long long chunk = sched_next(v, nchunks, total_warps, rank, first);
-    if (chunk < 0) break;
+    const long long claimed = sched_next(v, nchunks, total_warps, rank, first);
+    if (claimed < 0) break;
+    // cluster modes: main chunks in the order k_chunk_order chose (longest
+    // quads first, snaked over the SMs); everything else in list order
+    const long long chunk = (ordered_mode<MODE>() && claimed < nch_main) ? perm[claimed] : claimed;
     const bool is_long = chunk < nch_long;
     const bool is_main = chunk < nch_main;
     const int T = is_main ? 1 : is_long ? T_rest : T_short;
@@ -720,6 +811,10 @@ void launch_engine_mode(const Dev& v, const Grid& g, cudaStream_t s, int64_t n_t
     k_sched_reset<<<1, kSchedSlots, 0, s>>>(v);
     count_launch();
     k_root32<<<g.nsm * kRoot32CtasPerSm, 128, 0, s>>>(v);
+    count_launch();
+  }
+  if (ordered_mode<MODE>()) {
+    k_chunk_order<MODE><<<1, kOrderThreads, 0, s>>>(v);
     count_launch();
   }
   k_sched_reset<<<1, kSchedSlots, 0, s>>>(v);

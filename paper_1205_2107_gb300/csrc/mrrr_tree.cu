@@ -401,10 +401,12 @@ __global__ void k_childrep_first(Dev v) {
 // ladder of child_shift; the first candidate in ladder order whose growth
 // max|D+| is at most 8 spdiam is taken, else the one with the smallest
 // growth among these and the first candidate (counted in the diagnostics).
-// When the pool has room every candidate stores into rows of its own and
-// the winner's rows become the child, in one pass; otherwise the pass
-// measures growth only and the chosen transform is computed again with
-// stores into the rows reserved in phase 1 (which hold candidate 0's).
+// Every candidate stores into rows of its own -- in the pool when it has
+// room (the winner's rows become the child), else in the eigenvector
+// scratch (the warp copies the winner's rows over the node's) -- in one
+// pass; when neither has room the pass measures growth only and the chosen
+// transform is computed again with stores into the rows reserved in phase 1
+// (which hold candidate 0's).
 constexpr int kPhase2Group = 8;
 __constant__ int kPhase2Cands[kPhase2Group] = {1, 2, 3, 4, 8, 9, 18, 19};
 
@@ -427,7 +429,7 @@ __global__ void k_childrep(Dev v) {
     double g = INFINITY, sigma = 0.0, Rc = 0.0;
     int cand = 0;
     Node p{};
-    int64_t base = -1;
+    int64_t base = -1, sbase = -1;
     if (mine && gl == 0) {
       const int m = v.blk[c.block].m;
       const int64_t rows = (int64_t)kPhase2Group * m;
@@ -436,16 +438,23 @@ __global__ void k_childrep(Dev v) {
         atomicMax((unsigned long long*)&v.ctl->pool_need, (unsigned long long)(base + rows));
         if (base + rows > v.pool_cap) base = -1;
       }
+      if (base < 0) {  // else in the eigenvector scratch
+        const int64_t at = (int64_t)atomicAdd((unsigned long long*)&v.ctl->cand_top, (unsigned long long)rows);
+        if (at + rows <= cand_capacity(v)) sbase = at;
+      }
     }
     base = __shfl_sync(0xffffffffu, base, leader);
+    sbase = __shfl_sync(0xffffffffu, sbase, leader);
+    int m = 0;
     if (mine) {
       p = v.node[c.parent];
-      const int m = v.blk[c.block].m;
+      m = v.blk[c.block].m;
       cand = kPhase2Cands[gl];
       sigma = child_shift(cand, v.lo[c.first], v.hi[c.last], p.pivmin);
-      const int64_t at = base >= 0 ? base + (int64_t)gl * m : 0;
-      Rc = dstqds_child_pred(v.rep_dl + p.rep, v.rep_ul + p.rep, v.rep_dl + at, v.rep_ul + at, m, sigma, p.pivmin,
-                             base >= 0, &g);
+      double2* odl = base >= 0 ? v.rep_dl + base + (int64_t)gl * m : cand_dl(v) + max(sbase, (int64_t)0) + (int64_t)gl * m;
+      double2* oul = base >= 0 ? v.rep_ul + base + (int64_t)gl * m : cand_ul(v) + max(sbase, (int64_t)0) + (int64_t)gl * m;
+      Rc = dstqds_child_pred(v.rep_dl + p.rep, v.rep_ul + p.rep, odl, oul, m, sigma, p.pivmin,
+                             base >= 0 || sbase >= 0, &g);
     }
     const unsigned gbits = 0xffu << leader;
     const bool ok = mine && g <= 8.0 * c.spdiam;
@@ -470,15 +479,35 @@ __global__ void k_childrep(Dev v) {
         if (kPhase2Cands[k] == pick) pl = k;
     }
     const double R_pick = __shfl_sync(0xffffffffu, Rc, leader + max(pl, 0));
+    // winners stored in the scratch: the whole warp copies their rows over
+    // the node's rows (which held candidate 0), one node after the other
+    {
+      const bool cp = mine && gl == 0 && base < 0 && sbase >= 0 && pl >= 0;
+      __syncwarp();  // the candidates' stores are visible to the whole warp
+      unsigned todo = __ballot_sync(0xffffffffu, cp);
+      while (todo) {
+        const int src = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const int64_t dst = __shfl_sync(0xffffffffu, c.rep, src);
+        const int mm = __shfl_sync(0xffffffffu, m, src);
+        const int64_t from = __shfl_sync(0xffffffffu, sbase, src) + (int64_t)__shfl_sync(0xffffffffu, pl, src) * mm;
+        for (int i = lane; i < mm; i += 32) {
+          v.rep_dl[dst + i] = cand_dl(v)[from + i];
+          v.rep_ul[dst + i] = cand_ul(v)[from + i];
+        }
+      }
+      __syncwarp();
+    }
     if (!mine || gl != 0) continue;
     if (!okmask) diag(v.ctl, DIAG_CHILD_GROWTH);
-    const int m = v.blk[c.block].m;
     const int pick = pl < 0 ? 0 : kPhase2Cands[pl];
     const double sig = child_shift(pick, v.lo[c.first], v.hi[c.last], p.pivmin);
     if (pl < 0) {  // candidate 0: its rows and largest entry from phase 1
       set_child(v, id, c, p, c.rep, sig, c.pivmin);
     } else if (base >= 0) {
       set_child(v, id, c, p, base + (int64_t)pl * m, sig, R_pick);
+    } else if (sbase >= 0) {  // copied over the node's rows above
+      set_child(v, id, c, p, c.rep, sig, R_pick);
     } else {
       const double R = dstqds_child<true>(v.rep_dl + p.rep, v.rep_ul + p.rep, v.rep_dl + c.rep, v.rep_ul + c.rep, m,
                                           sig, p.pivmin);
