@@ -44,7 +44,10 @@ BISECT_FLOPS_PER_ROW = 4 * 32
 PATH_FLOPS_PER_ROW = BISECT_FLOPS_PER_ROW + 15
 ENGINE_STAGES = ("bisect_root", "prerefine", "refine", "final_bisect")
 DIV_COST_DFMA = 9.0  # DFMA-equivalents of one FP64 division; replaced by the measured ratio
-ENGINE_BYTES_PER_CHILD_ROW = 32  # engine DRAM traffic per child-representation row (ncu, W+ n=2001)
+# DRAM bytes (read + write) of the interval engine's launches over one clustered
+# step, measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum, one pass)
+# on the direct-launch batched solve of the same two matrices
+ENGINE_DRAM_BYTES_PER_STEP = 128.997e9
 
 
 def _hbm_gbs() -> float:
@@ -461,10 +464,12 @@ def run_ours(args, rank: int, world: int):
         achieved = BISECT_FLOPS_PER_ROW * nk / (engine_ms * 1e-3) / 1e9
         roof = {"bound": "alu", "kernel": "k_engine (interval bisection, all modes)", "achieved": achieved,
                 "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS,
-                "traffic": ENGINE_BYTES_PER_CHILD_ROW * max(child_rows, 0),
-                "traffic_source": "DRAM bytes per step, scaled from the ncu capture of W+ n=2001 (64.9 MB over its "
-                                  "6 engine launches = 31 bytes per child-representation row: refine and final "
-                                  "each read every child row once) by the step's child rows",
+                "traffic": ENGINE_DRAM_BYTES_PER_STEP,
+                "traffic_source": "DRAM bytes per step of the engine's 8 launches, one ncu capture of this "
+                                  "workload (profiles/k_engine_dram_bench_clustered_n20000.md): 129 GB, nearly "
+                                  "all reads of child representations (each pass of a warp streams its nodes' "
+                                  "rows; the 10,000+ first-level child representations, 3.2 GB, exceed L2)",
+                "child_rows": child_rows,
                 "engine_ms_per_step": engine_ms,
                 "peak_source": "measured on this GPU by mrrr_probe_peak (FP64 FMA throughput, all SMs)"}
     # whole path against T_roof = max(F / P_fp64, 8 n k / BW), F = 143 n k
