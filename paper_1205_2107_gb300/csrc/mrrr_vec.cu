@@ -30,6 +30,7 @@ namespace {
 constexpr int kRowAhead = 4;    // representation and scratch rows loaded ahead of the recurrences
 constexpr int kVecWarps = 4;    // 128 threads per CTA
 constexpr int kStageRows = 16;  // rows of z staged per lane before a coalesced flush
+constexpr int kPairAhead = 8;   // scratch rows loaded ahead in the two-lane form's gamma and solve sweeps
 
 // The 32 vectors of a warp are computed in row lockstep: every sweep runs over
 // the rows in the same order for all lanes (a lane idles on rows outside its
@@ -151,7 +152,9 @@ __device__ void twisted_warp(const VecLane& q, double* __restrict__ A, double* _
   // solve N_r z = gamma_r e_r with z_r = 1: upward z_i = -L+_i z_{i+1}
   // (i < r), downward z_{i+1} = -U-_i z_i (i >= r)
   if (act) q.zc[r] = 1.0;
-  double n2 = 1.0;
+  // ||z||^2 = (1 + upper part) + lower part, each part summed away from r
+  // (the order the two-lane form of twisted_pair uses as well)
+  double up = 0.0, down = 0.0;
   int R = act ? r : 0;
   for (int o = 16; o; o >>= 1) R = max(R, __shfl_xor_sync(0xffffffffu, R, o));
   double z = 1.0;
@@ -171,7 +174,7 @@ __device__ void twisted_warp(const VecLane& q, double* __restrict__ A, double* _
       if (i >= 0) {
         if (act && i < r) {
           z = -a * z;
-          n2 = fma(z, z, n2);
+          up = fma(z, z, up);
           stage[i & (kStageRows - 1)][lane] = z;
         }
         if ((i & (kStageRows - 1)) == 0) flush_stage(stage, i, q.zc, 0, r - 1, lane);
@@ -198,7 +201,7 @@ __device__ void twisted_warp(const VecLane& q, double* __restrict__ A, double* _
         const int j = i + 1;
         if (act && i >= r && i <= m - 2) {
           z = -b * z;
-          n2 = fma(z, z, n2);
+          down = fma(z, z, down);
           stage[j & (kStageRows - 1)][lane] = z;
         }
         if ((j & (kStageRows - 1)) == kStageRows - 1 || j == M - 1)
@@ -208,11 +211,152 @@ __device__ void twisted_warp(const VecLane& q, double* __restrict__ A, double* _
   }
   r_out = r;
   gamma_out = gamma;
-  norm2_out = n2;
+  norm2_out = (1.0 + up) + down;
+}
+
+// The same twisted factorization with two lanes per vector (lane pairs
+// 2k, 2k+1 of the warp), for vectors too few to fill the GPU, where the
+// recurrences' latency, not the FP64 pipe, sets the time.  Both lanes run
+// one instruction stream on different rows:
+//   1. the even ("top") lane the stationary transform top-down (L+ and s
+//      into its scratch), the odd ("bottom") lane the progressive transform
+//      bottom-up (U- and p into its scratch) -- one recurrence each,
+//      x = a + s, q = b / x, out = c1 q, s <- c2 s q - lam, with
+//      (a, b, c1, c2) = (D, LD, 1, l) top and (LLD, D, l, 1) bottom;
+//   2. gamma_i = s_i + p_i + lam over the lower half of the rows (top) and
+//      the upper half (bottom), each reading its own and its partner's
+//      scratch, and r = argmin |gamma_i| (lowest index on ties);
+//   3. the solve from z_r = 1, upward with L+ (top) and downward with U-
+//      (bottom), z stored directly.
+// Every value is computed by the same operations in the same order as in
+// twisted_warp, so the vector, gamma_r and ||z||^2 come out bit for bit the
+// same.  Returns r, gamma_r and ||z||^2 in both lanes.
+__device__ __noinline__ void twisted_pair(const VecLane& q, double* __restrict__ A, double* __restrict__ B, int64_t nthr,
+                             int lane, int& r_out, double& gamma_out, double& norm2_out) {
+  const bool top = (lane & 1) == 0;
+  const bool act = q.m > 0;
+  const int m = q.m;
+  int M = m;
+  for (int o = 16; o; o >>= 1) M = max(M, __shfl_xor_sync(0xffffffffu, M, o));
+  const double lam = q.lam, pivmin = q.pivmin;
+  // partner's scratch columns (the pair's threads are neighbours)
+  const double* Bp = top ? B + 1 : B - 1;
+  // 1. the two transforms, row i = k (top) or m - 2 - k (bottom)
+  double s = top ? -lam : (act ? q.dl[m - 1].x - lam : 0.0);
+  if (act && !top) B[(int64_t)(m - 1) * nthr] = s;  // p_{m-1}
+  double2 pd[kRowAhead], pu[kRowAhead];
+#pragma unroll
+  for (int u = 0; u < kRowAhead; ++u) {
+    const int i = top ? u : m - 2 - u;
+    const bool ok = act && u < m - 1;
+    pd[u] = ok ? __ldg(q.dl + i) : make_double2(0.0, 0.0);
+    pu[u] = ok ? __ldg(q.ul + i) : make_double2(0.0, 0.0);
+  }
+  for (int k0 = 0; k0 < M - 1; k0 += kRowAhead) {
+#pragma unroll
+    for (int u = 0; u < kRowAhead; ++u) {
+      const int k = k0 + u;
+      const double2 xd = pd[u], xu = pu[u];
+      const int knext = k + kRowAhead;
+      const bool oknext = act && knext < m - 1;
+      const int inext = top ? knext : m - 2 - knext;
+      pd[u] = oknext ? __ldg(q.dl + inext) : make_double2(0.0, 0.0);
+      pu[u] = oknext ? __ldg(q.ul + inext) : make_double2(0.0, 0.0);
+      if (act && k < m - 1) {
+        const int i = top ? k : m - 2 - k;
+        const double a = top ? xd.x : xd.y;   // D | LLD
+        const double b = top ? xu.y : xd.x;   // LD | D
+        double x = a + s;
+        if (fabs(x) < pivmin) x = -pivmin;
+        const double qq = b / x;
+        A[(int64_t)i * nthr] = top ? qq : xu.x * qq;  // L+ | U- = l D / D-
+        const double s_new = top ? fma(qq, xu.x * s, -lam) : fma(s, qq, -lam);
+        B[(int64_t)i * nthr] = top ? s : s_new;       // s_i | p_i
+        s = s_new;
+      }
+    }
+  }
+  if (act && top) B[(int64_t)(m - 1) * nthr] = s;  // s_{m-1}
+  __syncwarp();  // the partner's stores are visible
+  // 2. gamma over the two halves; r = argmin |gamma|, lowest index on ties
+  const int h = m / 2;
+  const int lo = top ? 0 : h, hi = top ? h : m;
+  int H = act ? hi - lo : 0;
+  for (int o = 16; o; o >>= 1) H = max(H, __shfl_xor_sync(0xffffffffu, H, o));
+  double best = INFINITY, gamma = 0.0;
+  int r = m;
+  double so[kPairAhead], sp[kPairAhead];  // own and partner rows, loaded ahead
+#pragma unroll
+  for (int u = 0; u < kPairAhead; ++u) {
+    const bool ok = act && lo + u < hi;
+    so[u] = ok ? B[(int64_t)(lo + u) * nthr] : 0.0;
+    sp[u] = ok ? Bp[(int64_t)(lo + u) * nthr] : 0.0;
+  }
+  for (int j0 = 0; j0 < H; j0 += kPairAhead) {
+#pragma unroll
+    for (int u = 0; u < kPairAhead; ++u) {
+      const int i = lo + j0 + u;
+      const double own = so[u], other = sp[u];
+      const int inext = i + kPairAhead;
+      const bool ok = act && inext < hi;
+      so[u] = ok ? B[(int64_t)inext * nthr] : 0.0;
+      sp[u] = ok ? Bp[(int64_t)inext * nthr] : 0.0;
+      if (act && i < hi) {
+        const double g = (top ? own + other : other + own) + lam;  // (s_i + p_i) + lam
+        const double ag = fabs(g);
+        if (ag < best || (ag == best && i < r)) {
+          best = ag;
+          r = i;
+          gamma = g;
+        }
+      }
+    }
+  }
+  {
+    const double ob = __shfl_xor_sync(0xffffffffu, best, 1);
+    const int orr = __shfl_xor_sync(0xffffffffu, r, 1);
+    const double og = __shfl_xor_sync(0xffffffffu, gamma, 1);
+    if (ob < best || (ob == best && orr < r)) {
+      best = ob;
+      r = orr;
+      gamma = og;
+    }
+  }
+  if (act && r >= m) r = m - 1;  // no comparable gamma: the last row, as the one-lane form starts
+  // 3. the solve: upward (top) rows r-1 .. 0 with L+, downward (bottom)
+  // rows r+1 .. m-1 with U-
+  if (act && top) q.zc[r] = 1.0;
+  const int len = act ? (top ? r : m - 1 - r) : 0;
+  int L = len;
+  for (int o = 16; o; o >>= 1) L = max(L, __shfl_xor_sync(0xffffffffu, L, o));
+  double z = 1.0, acc = 0.0;
+  double av[kPairAhead];  // L+ / U- rows, loaded ahead
+#pragma unroll
+  for (int u = 0; u < kPairAhead; ++u) av[u] = u < len ? A[(int64_t)(top ? r - 1 - u : r + u) * nthr] : 0.0;
+  for (int j0 = 0; j0 < L; j0 += kPairAhead) {
+#pragma unroll
+    for (int u = 0; u < kPairAhead; ++u) {
+      const int j = j0 + u;
+      const double a = av[u];
+      const int jn = j + kPairAhead;
+      av[u] = jn < len ? A[(int64_t)(top ? r - 1 - jn : r + jn) * nthr] : 0.0;
+      if (j < len) {
+        const int i = top ? r - 1 - j : r + j;  // scratch row
+        z = -a * z;
+        acc = fma(z, z, acc);
+        q.zc[top ? i : i + 1] = z;
+      }
+    }
+  }
+  const double oacc = __shfl_xor_sync(0xffffffffu, acc, 1);
+  const double upp = top ? acc : oacc, dwn = top ? oacc : acc;
+  r_out = r;
+  gamma_out = gamma;
+  norm2_out = (1.0 + upp) + dwn;
 }
 
 template <bool RQ>
-__global__ void __launch_bounds__(kVecWarps * 32) k_vectors(Dev v) {
+__global__ void __launch_bounds__(kVecWarps * 32, 4) k_vectors(Dev v) {
   __shared__ double stage_all[kVecWarps][kStageRows][33];
   const int lane = threadIdx.x & 31;
   double (*stage)[33] = stage_all[threadIdx.x >> 5];
@@ -221,16 +365,25 @@ __global__ void __launch_bounds__(kVecWarps * 32) k_vectors(Dev v) {
   double* B = v.vscr + tid;
   double* A = v.vscr + v.vscr_threads * v.vscr_rows + tid;
   unsigned long long iters = 0;
-  // chunks of 32 consecutive slots (one per lane), spread over the SM
-  // sub-partitions by the scheduler; every lane of a warp works on the same
-  // chunk (warp-wide sweeps)
-  const long long nchunks = (nslots + 31) / 32;
+  // chunks spread over the SM sub-partitions by the scheduler; every lane of
+  // a warp works on the same chunk (warp-wide sweeps).  Whole waves (every
+  // sub-partition the same number) of chunks of 32 consecutive slots, one
+  // per lane; the slots past them in chunks of 16, two lanes per slot
+  // (twisted_pair), which halves the length of the chunks that run where
+  // the others have finished -- and of all chunks when the vectors are too
+  // few for one wave.
+  const long long wave = (long long)v.nsm * 4 * 32;
+  const long long nmain = (nslots / wave) * wave;
+  const long long nch_main = nmain / 32;
+  const long long nchunks = nch_main + (nslots - nmain + 15) / 16;
   const long long rank = sched_rank(v);
   bool first = true;
   for (;;) {
     const long long chunk = sched_next(v, nchunks, nthr / 32, rank, first);
     if (chunk < 0) break;
-    const int64_t w = chunk * 32 + lane;
+    const bool pair = chunk >= nch_main;
+    const bool lead = !pair || (lane & 1) == 0;  // the lane that writes a slot's results
+    const int64_t w = pair ? nmain + (chunk - nch_main) * 16 + (lane >> 1) : chunk * 32 + lane;
     VecLane q{};
     int st = w < nslots ? v.state[w] : 0;
     const bool has = (st == SLOT_SINGLETON || st == SLOT_FALLBACK || st == SLOT_TRIVIAL) && v.spos[w] >= 0;
@@ -245,11 +398,13 @@ __global__ void __launch_bounds__(kVecWarps * 32) k_vectors(Dev v) {
       const int m = bk.m;
       double* zc = v.Z ? v.Z + pr.zout + (int64_t)pos * pr.ldz + (bk.row0 - pr.row0) : nullptr;
       if (st == SLOT_TRIVIAL || m == 1) {
-        v.W[pr.wout + pos] = nd.sigma_abs / pr.scale;
-        if (zc) zc[0] = 1.0;
-        v.znrm2[w] = 1.0;
+        if (lead) {
+          v.W[pr.wout + pos] = nd.sigma_abs / pr.scale;
+          if (zc) zc[0] = 1.0;
+          v.znrm2[w] = 1.0;
+        }
       } else if (!zc) {  // eigenvalues only: the bisected value is final
-        v.W[pr.wout + pos] = (nd.sigma_abs + 0.5 * (v.lo[w] + v.hi[w])) / pr.scale;
+        if (lead) v.W[pr.wout + pos] = (nd.sigma_abs + 0.5 * (v.lo[w] + v.hi[w])) / pr.scale;
       } else {
         // the eigenvalue was bisected to full relative accuracy on this
         // representation: one twisted factorization gives the vector
@@ -272,12 +427,15 @@ __global__ void __launch_bounds__(kVecWarps * 32) k_vectors(Dev v) {
     const double blo = (RQ && q.m > 0) ? v.lo[w] : 0.0;
     const double bhi = (RQ && q.m > 0) ? v.hi[w] : 0.0;
     for (int it = 0;; ++it) {
-      twisted_warp(q, A, B, nthr, stage, lane, r, gamma, n2);
+      if (pair)
+        twisted_pair(q, A, B, nthr, lane, r, gamma, n2);
+      else
+        twisted_warp(q, A, B, nthr, stage, lane, r, gamma, n2);
       if (!RQ) break;
       if (q.m > 0) q.lam = fmin(fmax(q.lam + gamma / n2, blo), bhi);
       if (it >= v.rq_steps) break;
     }
-    if (q.m > 0) {
+    if (q.m > 0 && lead) {
       iters += 1 + v.rq_steps;
       if (!isfinite(n2)) set_status(v.ctl, MRRR_ERR_NOCONV);
       v.W[pr.wout + pos] = (nd.sigma_abs + q.lam) / pr.scale;
