@@ -120,9 +120,11 @@ typedef struct mrrr_options {
   int singleton_rq;        /* Rayleigh-quotient correction of singletons (Sec. 3.1.1: the
                               vector stage may improve an eigenvalue): k = 1..4 (default 1)
                               bisects each singleton to 2^-36 relative only, then takes
-                              k + 1 twisted factorizations, each moving lambda by the
-                              Rayleigh quotient gamma_r / ||z||^2 of the last (kept inside
-                              the bisection bracket); the vector is the last one's and
+                              up to k + 1 twisted factorizations (at least two), each
+                              moving lambda by the Rayleigh quotient gamma_r / ||z||^2 of
+                              the last (kept inside the bisection bracket), stopping
+                              early once the corrections of a warp's vectors are all
+                              below 2 eps |lambda|; the vector is the last one's and
                               lambda its Rayleigh quotient.  -1: no correction, every
                               singleton bisected to full relative accuracy (2 eps) and one
                               twisted factorization.  Ignored with vector_precision 2

@@ -423,20 +423,29 @@ __global__ void __launch_bounds__(kVecWarps * 32, 4) k_vectors(Dev v) {
     // gamma_r z_r with z_r = 1, so lam + gamma_r / ||z||^2 is the Rayleigh
     // quotient of the last vector; each new value, kept inside the
     // bisection bracket, gets a new twisted factorization, and the last
-    // one's quotient is the eigenvalue.
+    // one's quotient is the eigenvalue.  After the second factorization
+    // the warp stops early once no lane's correction exceeds 2 eps |lam|
+    // (converged: a further factorization would repeat the vector).
     const double blo = (RQ && q.m > 0) ? v.lo[w] : 0.0;
     const double bhi = (RQ && q.m > 0) ? v.hi[w] : 0.0;
+    int nfact = 0;
     for (int it = 0;; ++it) {
       if (pair)
         twisted_pair(q, A, B, nthr, lane, r, gamma, n2);
       else
         twisted_warp(q, A, B, nthr, stage, lane, r, gamma, n2);
+      ++nfact;
       if (!RQ) break;
-      if (q.m > 0) q.lam = fmin(fmax(q.lam + gamma / n2, blo), bhi);
-      if (it >= v.rq_steps) break;
+      bool small = true;
+      if (q.m > 0) {
+        const double nl = fmin(fmax(q.lam + gamma / n2, blo), bhi);
+        small = fabs(nl - q.lam) <= 2.0 * kEps * fabs(q.lam);
+        q.lam = nl;
+      }
+      if (it >= v.rq_steps || (it >= 1 && __all_sync(0xffffffffu, small))) break;
     }
     if (q.m > 0 && lead) {
-      iters += 1 + v.rq_steps;
+      iters += nfact;
       if (!isfinite(n2)) set_status(v.ctl, MRRR_ERR_NOCONV);
       v.W[pr.wout + pos] = (nd.sigma_abs + q.lam) / pr.scale;
       v.wval[w] = q.lam;

@@ -242,7 +242,9 @@ def test_singleton_rq_takes_one_more_factorization_per_step():
         plan = api.Plan(singleton_rq=steps)
         solve(d, e, plan=plan)
         counts.append(plan.info()["twisted_solves"])
-    assert counts[1] == 2 * counts[0] and counts[2] == 3 * counts[0]
+    # one correction: always a second factorization; two: a third unless
+    # every lane of a warp had converged after the second
+    assert counts[1] == 2 * counts[0] and 2 * counts[0] <= counts[2] <= 3 * counts[0]
 
 
 def test_singleton_rq_options_are_checked():
