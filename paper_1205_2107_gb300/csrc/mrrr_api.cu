@@ -159,7 +159,7 @@ constexpr int kSliceWidth = 4;  // multisection width of slice calls unless the 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-  size_t ctl, prob, blk, node, pool_dl, pool_ul, ilist, lwin, sched_cnt, sched_claim, lo, hi, gap, wval, znrm2,
+  size_t ctl, prob, blk, node, pool_dl, pool_ul, ilist, lwin, rgrid, sched_cnt, sched_claim, lo, hi, gap, wval, znrm2,
       snode, sj, spos, state, bflag, vscr;
   size_t total;
   int64_t max_blocks, max_nodes, max_slots, pool_rows, vscr_threads, vscr_rows;
@@ -214,6 +214,7 @@ Layout make_layout(const mrrr_plan* p, int batch, int64_t n_total, int64_t k_tot
   L.pool_ul = take(sizeof(double2) * (size_t)L.pool_rows);
   L.ilist = take(sizeof(int64_t) * (size_t)L.max_slots);
   L.lwin = take(sizeof(int64_t) * 2 * (size_t)((L.max_slots + 31) / 32));
+  L.rgrid = take(sizeof(int) * 2 * (size_t)std::max<int64_t>(n_total, 1));
   L.sched_cnt = take(sizeof(int) * (size_t)kSchedSlots);
   L.sched_claim = take(sizeof(int) * (size_t)L.max_slots);
 
@@ -249,6 +250,7 @@ Dev make_dev(const mrrr_plan* p, const Layout& L, void* ws, int batch, const dou
   v.rep_ul = reinterpret_cast<double2*>(b + L.pool_ul);
   v.ilist = reinterpret_cast<int64_t*>(b + L.ilist);
   v.lwin = reinterpret_cast<int64_t*>(b + L.lwin);
+  v.rgrid = reinterpret_cast<int*>(b + L.rgrid);
   v.sched_cnt = reinterpret_cast<int*>(b + L.sched_cnt);
   v.sched_claim = reinterpret_cast<int*>(b + L.sched_claim);
   v.max_chunks = L.max_slots;

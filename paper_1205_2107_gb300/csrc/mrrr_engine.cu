@@ -453,9 +453,10 @@ __device__ __forceinline__ int width_for(long long nlist, long long lanes_total,
 
 // Starting brackets for the FP32 bisection: for every root block of at
 // least kGridMinRows rows, FP32 counts at kGridPoints - 1 evenly spaced
-// interior points of its Gershgorin bracket (one thread each), kept in the
-// eigenvector scratch after the FP32 rows (ints at 2 row0 of the block, so
-// blocks never overlap).  An interval then starts from the grid cell whose
+// interior points of its Gershgorin bracket (one thread each), kept at
+// 2 row0 of the block in an array of 2 ints per row of T (blocks never
+// overlap).  The grid depends on the block alone, so an interval's starting
+// bracket is the same whichever call, batch or slice computes it.  An interval then starts from the grid cell whose
 // counts bracket its index instead of the whole Gershgorin bracket: about
 // ten halvings fewer.  Counts that rounding made non-monotone can only give
 // a wrong cell, which the FP64 check of the bracket widens as it would any
@@ -467,18 +468,9 @@ __device__ __forceinline__ float grid_point(float gl, float gu, int g) {
   return gl + (gu - gl) * ((float)g / (float)kGridPoints);
 }
 
-__device__ __forceinline__ int* grid_counts(const Dev& v, int64_t n_total, int64_t row0) {
-  return reinterpret_cast<int*>(v.vscr + n_total) + 2 * row0;
-}
+__device__ __forceinline__ int* grid_counts(const Dev& v, int64_t row0) { return v.rgrid + 2 * row0; }
 
-// Whether the scratch holds the grid (the FP32 rows, n_total doubles, then
-// up to 2 n_total ints).
-__device__ __forceinline__ bool grid_fits(const Dev& v, int64_t n_total) {
-  return 2 * n_total <= (int64_t)v.vscr_threads * v.vscr_rows * (v.vec_dd ? 4 : 2);
-}
-
-__global__ void __launch_bounds__(kGridPoints) k_root32_grid(Dev v, int64_t n_total) {
-  if (!grid_fits(v, n_total) || v.fixed_width > 0) return;
+__global__ void __launch_bounds__(kGridPoints) k_root32_grid(Dev v) {
   const float2* rows = root32_rows(v);
   const int nblocks = v.ctl->nblocks;
   for (int b = blockIdx.x; b < nblocks; b += gridDim.x) {
@@ -486,7 +478,7 @@ __global__ void __launch_bounds__(kGridPoints) k_root32_grid(Dev v, int64_t n_to
     if (bk.m < kGridMinRows || bk.je < bk.js) continue;
     const int g = threadIdx.x + 1;
     if (g < kGridPoints)
-      grid_counts(v, n_total, bk.row0)[g] =
+      grid_counts(v, bk.row0)[g] =
           negcount32(rows + bk.row0, bk.m, grid_point((float)bk.gl, (float)bk.gu, g));
   }
 }
@@ -501,7 +493,7 @@ __global__ void __launch_bounds__(kGridPoints) k_root32_grid(Dev v, int64_t n_to
 // its bracket does not depend on the list it is in.
 constexpr int kRoot32CtasPerSm = 4;
 
-__global__ void __launch_bounds__(128) k_root32(Dev v, int64_t n_total) {
+__global__ void __launch_bounds__(128) k_root32(Dev v) {
   const int lane = threadIdx.x & 31;
   const long long nlist = min(v.ctl->nlist, (long long)v.max_list);
   const float2* rows = root32_rows(v);
@@ -515,7 +507,6 @@ __global__ void __launch_bounds__(128) k_root32(Dev v, int64_t n_total) {
   const long long nchunks = nch_main + (nlist - nmain + g_rest - 1) / g_rest;
   const long long total_warps = (long long)gridDim.x * (blockDim.x / 32);
   const long long rank = sched_rank(v);
-  const bool use_grid = !fixed && grid_fits(v, n_total);
   bool first = true;
   for (;;) {
     const long long chunk = sched_next(v, nchunks, total_warps, rank, first);
@@ -536,8 +527,8 @@ __global__ void __launch_bounds__(128) k_root32(Dev v, int64_t n_total) {
       row0 = bk.row0;
       lo = (float)bk.gl;
       hi = (float)bk.gu;
-      if (use_grid && m >= kGridMinRows) {  // the grid cell whose counts bracket j
-        const int* c = grid_counts(v, n_total, row0);
+      if (m >= kGridMinRows) {  // the grid cell whose counts bracket j
+        const int* c = grid_counts(v, row0);
         int a = 1, z = kGridPoints;  // first point g in [1, kGridPoints) with count >= j, else kGridPoints
         while (a < z) {
           const int mid = (a + z) >> 1;
@@ -865,9 +856,9 @@ void launch_engine_mode(const Dev& v, const Grid& g, cudaStream_t s, int64_t n_t
     count_launch();
     k_sched_reset<<<1, kSchedSlots, 0, s>>>(v);
     count_launch();
-    k_root32_grid<<<g.slot_blocks, kGridPoints, 0, s>>>(v, n_total);
+    k_root32_grid<<<g.slot_blocks, kGridPoints, 0, s>>>(v);
     count_launch();
-    k_root32<<<g.nsm * kRoot32CtasPerSm, 128, 0, s>>>(v, n_total);
+    k_root32<<<g.nsm * kRoot32CtasPerSm, 128, 0, s>>>(v);
     count_launch();
   }
   if (ordered_mode<MODE>()) {

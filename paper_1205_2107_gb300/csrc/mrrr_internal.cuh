@@ -145,6 +145,7 @@ struct Dev {
   int64_t* ilist;     // work list of the interval engine (slot indices)
   int64_t max_list;
   int64_t* lwin;      // per 32-slot window: offsets of its long and short entries in the list
+  int* rgrid;         // FP32 root counts on a grid per block (2 ints per row of T)
   int* sched_cnt;     // chunk scheduler: warps seen per SM sub-partition (kSchedSlots)
   int* sched_claim;   //   per chunk: generation of the launch that claimed it
   int64_t max_chunks;
