@@ -284,10 +284,9 @@ def run_ours(args, rank: int, world: int):
     lay = api.BatchLayout(sizes, dev)
     d_cat = torch.tensor(np.concatenate([d for _, d, _ in mats]), device=dev)
     e_cat = torch.tensor(np.concatenate([np.append(e, 0.0) for _, _, e in mats]), device=dev)
-    # pinned host buffers of the end-to-end leg, allocated first and written
-    # once from the CPU: on the GB300 host, 6.4 GB copies into pinned buffers
-    # allocated late in the process (after the other legs' allocations) ran at
-    # 14-40 GB/s instead of the 193 GB/s of buffers allocated early (measured)
+    # pinned host buffers of the end-to-end leg, allocated once up front and
+    # written once from the CPU (D2H copies into them have ranged from 14 to
+    # 193 GB/s between runs on the GB300 host; the pipeline below hides that)
     host_bufs = (d_cat.cpu().pin_memory(), e_cat.cpu().pin_memory(),
                  [torch.zeros(lay.k_total, dtype=torch.float64, pin_memory=True) for _ in range(2)],
                  [torch.zeros(lay.z_total, dtype=torch.float64, pin_memory=True) for _ in range(2)])

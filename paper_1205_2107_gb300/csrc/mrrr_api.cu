@@ -177,8 +177,9 @@ int64_t vec_threads(const mrrr_plan* p, int64_t max_slots, int n_max) {
   const int64_t waves = (max_slots + per_wave - 1) / per_wave;
   const int64_t row_bytes = p->opt.vector_precision == 2 ? 32 : 16;  // scratch per row and thread
   const int64_t mem_c = ((int64_t)32 << 30) / (row_bytes * (int64_t)std::max(n_max, 1)) / per_wave;
-  const int64_t c = std::max<int64_t>(1, std::min<int64_t>({waves, (int64_t)std::max(1, p->opt.vec_blocks_per_sm),
-                                                           mem_c}));
+  // at most 4: the eigenvector kernel runs 4 CTAs of 128 threads per SM
+  const int64_t c = std::max<int64_t>(
+      1, std::min<int64_t>({waves, (int64_t)std::min(4, std::max(1, p->opt.vec_blocks_per_sm)), mem_c}));
   return per_wave * c;
 }
 

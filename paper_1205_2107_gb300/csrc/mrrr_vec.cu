@@ -29,6 +29,7 @@ namespace {
 
 constexpr int kRowAhead = 4;    // representation and scratch rows loaded ahead of the recurrences
 constexpr int kVecWarps = 4;    // 128 threads per CTA
+constexpr int kVecCtasPerSm = 4;  // what the register cap (128) lets reside: every SM full
 constexpr int kStageRows = 16;  // rows of z staged per lane before a coalesced flush
 constexpr int kPairAhead = 8;   // scratch rows loaded ahead in the two-lane form's gamma and solve sweeps
 
@@ -360,10 +361,18 @@ __global__ void __launch_bounds__(kVecWarps * 32, 4) k_vectors(Dev v) {
   __shared__ double stage_all[kVecWarps][kStageRows][33];
   const int lane = threadIdx.x & 31;
   double (*stage)[33] = stage_all[threadIdx.x >> 5];
-  const int64_t tid = gtid(), nthr = gstride();
   const int64_t nslots = v.ctl->nslots;
-  double* B = v.vscr + tid;
-  double* A = v.vscr + v.vscr_threads * v.vscr_rows + tid;
+  // The grid fills every SM (kVecCtasPerSm CTAs, all resident), and the
+  // warps that work are the first vscr_threads / (32 x 4 SMs) on each SM
+  // sub-partition by the scheduler's rank: the same number on every
+  // sub-partition however the hardware placed the CTAs.  A working warp's
+  // scratch columns follow from its rank.
+  const long long rank = sched_rank(v);
+  const int64_t nthr = v.vscr_threads;  // scratch columns (the row stride)
+  if (rank >= nthr / 32) return;
+  const int64_t col = rank * 32 + lane;
+  double* B = v.vscr + col;
+  double* A = v.vscr + v.vscr_threads * v.vscr_rows + col;
   unsigned long long iters = 0;
   // chunks spread over the SM sub-partitions by the scheduler; every lane of
   // a warp works on the same chunk (warp-wide sweeps).  Whole waves (every
@@ -376,7 +385,6 @@ __global__ void __launch_bounds__(kVecWarps * 32, 4) k_vectors(Dev v) {
   const long long nmain = (nslots / wave) * wave;
   const long long nch_main = nmain / 32;
   const long long nchunks = nch_main + (nslots - nmain + 15) / 16;
-  const long long rank = sched_rank(v);
   bool first = true;
   for (;;) {
     const long long chunk = sched_next(v, nchunks, nthr / 32, rank, first);
@@ -899,9 +907,9 @@ void launch_vectors(const Dev& v, const Grid& g, cudaStream_t s) {
   if (v.vec_dd)
     k_vectors_dd<<<g.vec_blocks, 128, 0, s>>>(v);
   else if (v.rq_steps > 0)
-    k_vectors<true><<<g.vec_blocks, 128, 0, s>>>(v);
+    k_vectors<true><<<g.nsm * kVecCtasPerSm, kVecWarps * 32, 0, s>>>(v);
   else
-    k_vectors<false><<<g.vec_blocks, 128, 0, s>>>(v);
+    k_vectors<false><<<g.nsm * kVecCtasPerSm, kVecWarps * 32, 0, s>>>(v);
   count_launch();
   if (v.Z) {
     k_normalize<<<g.nsm * 16, 256, 0, s>>>(v);
