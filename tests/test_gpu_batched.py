@@ -175,3 +175,21 @@ def test_batched_equals_plain_bitwise_under_a_fixed_schedule(width):
         assert torch.equal(Ws[p], W1), f"problem {p}: W differs"
         assert torch.equal(Zs[p], Z1), f"problem {p}: Z differs"
         check_problem(d[off[p]:off[p + 1]], e[off[p]:off[p + 1]], W1, Z1, 1, n, compare_vectors=n <= 300)
+
+
+def test_one_lane_and_two_lane_vectors_are_bit_for_bit_alike():
+    """A batch with more vectors than one wave of the GPU's lanes computes
+    the first whole waves with one lane per vector and the rest with two
+    (twisted_pair); each problem alone has fewer vectors than a wave and
+    takes two lanes for all.  Under a fixed schedule the bits must agree."""
+    sizes = [1000] * 24  # 24,000 eigenpairs: more than 608 x 32 slots
+    d, e, off = inputs.batched_uniform(sizes, 123)
+    lay = api.BatchLayout(sizes, "cuda")
+    plan = api.Plan(multisection_width=4)
+    W, Z = api.eigh_tridiagonal_batched(_dev(d), _dev(e), lay, plan=plan)
+    Ws, Zs = lay.unpack(W, Z)
+    plan1 = api.Plan(multisection_width=4)
+    for p in (0, 5, 11, 17, 23):  # early problems in the one-lane waves, the last in the two-lane rest
+        W1, Z1 = api.eigh_tridiagonal(_dev(d[off[p]:off[p + 1]]), _dev(e[off[p]:off[p + 1]]), plan=plan1)
+        assert torch.equal(Ws[p], W1), f"problem {p}: W differs"
+        assert torch.equal(Zs[p], Z1), f"problem {p}: Z differs"

@@ -257,3 +257,15 @@ def test_singleton_rq_options_are_checked():
     plan = api.Plan(singleton_rq=2, vector_precision=2)
     assert_parity(d, e, plan=plan)
     assert plan.info()["twisted_solves"] == 2 * 300
+
+
+@pytest.mark.parametrize("rtol", [2.0 ** -13, 2.0 ** -20])
+@pytest.mark.parametrize("case", ["wilkinson_201", "glued_x10", "uniform_500"])
+def test_fp32_prebisection_width(case, rtol):
+    """The FP32 pre-bisection of the root intervals (option prebisect_rtol,
+    2^-17 by default) only moves halvings between the FP32 and FP64 pipes:
+    at its widest and narrowest setting the solve meets the same goals."""
+    d, e = RQ_CASES[case]()
+    plan = api.Plan(prebisect_rtol=rtol)
+    assert_parity(d, e, plan=plan)
+    assert plan.info()["status"] == 0
