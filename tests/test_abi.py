@@ -45,6 +45,7 @@ def test_options_defaults(lib):
     assert o.classify_rtol == 2.0 ** -20
     assert o.max_depth == 64 and o.threads_per_block % 32 == 0
     assert o.singleton_rq == 1 and o.vector_precision == 1
+    assert o.prebisect_rtol == 2.0 ** -17
     assert lib.mrrr_options_default(None) == _lib.ERR_ARG
 
 
@@ -143,3 +144,46 @@ def test_plain_c_client_links_and_runs(lib, tmp_path):
     out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
     assert out.returncode == 0, (out.returncode, out.stderr)
     assert out.stdout.strip() == f"version {lib.mrrr_version()}"
+
+
+LAYOUT_CLIENT = r"""
+#include <stddef.h>
+#include <stdio.h>
+#include "mrrr.h"
+
+#define F(T, m) printf(#T "." #m " %zu\n", offsetof(T, m))
+int main(void) {
+  printf("mrrr_options %zu\nmrrr_info %zu\nmrrr_tuning %zu\nmrrr_profile %zu\n", sizeof(mrrr_options),
+         sizeof(mrrr_info), sizeof(mrrr_tuning), sizeof(mrrr_profile));
+  F(mrrr_options, width_scale); F(mrrr_options, prebisect_rtol); F(mrrr_options, multisection_width);
+  F(mrrr_options, vector_precision); F(mrrr_options, singleton_rq); F(mrrr_options, reserved_);
+  F(mrrr_info, diag); F(mrrr_info, sturm_counts); F(mrrr_info, warp_passes);
+  F(mrrr_tuning, best_ms); F(mrrr_tuning, singleton_rq);
+  return 0;
+}
+"""
+
+
+def test_ctypes_structs_match_the_header(lib, tmp_path):
+    """The ctypes mirrors of the ABI structs have the header's sizes and
+    field offsets (a C compiler lays the header out; ctypes must agree, or
+    options and counters would be read from the wrong bytes)."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "layout.c"
+    src.write_text(LAYOUT_CLIENT)
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                    str(exe)], check=True, capture_output=True)
+    got = dict(line.rsplit(" ", 1) for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                              timeout=60).stdout.strip().splitlines())
+    mirrors = {"mrrr_options": _lib.Options, "mrrr_info": _lib.Info, "mrrr_tuning": _lib.Tuning,
+               "mrrr_profile": _lib.Profile}
+    for name, cls in mirrors.items():
+        assert int(got[name]) == ctypes.sizeof(cls), name
+    for key, value in got.items():
+        if "." in key:
+            struct, field = key.split(".")
+            assert int(value) == getattr(mirrors[struct], field).offset, key
