@@ -168,7 +168,13 @@ mrrr_status mrrr_options_default(mrrr_options* opt);
 
 /* Create a plan on the current CUDA device.  opt may be NULL (defaults).
    The plan owns a small pinned host buffer and its CUDA graphs; it is not
-   thread-safe: use one plan per host thread. */
+   thread-safe: use one plan per host thread.  Options out of range
+   (multisection_width not 0 or a power of two <= 32, root_side outside 0..2,
+   vector_precision outside 0..2, singleton_rq outside -1..4, gap_tol >= 1,
+   classify_rtol, cluster_rtol or prebisect_rtol >= 1/4, threads_per_block not
+   a multiple of 32, a non-finite root_perturb or width_scale) give
+   MRRR_ERR_ARG before any CUDA call, with *plan set to NULL (as on every
+   failure). */
 mrrr_status mrrr_plan_create(mrrr_plan** plan, const mrrr_options* opt);
 mrrr_status mrrr_plan_destroy(mrrr_plan* plan);
 

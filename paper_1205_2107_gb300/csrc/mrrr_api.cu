@@ -593,6 +593,9 @@ mrrr_status mrrr_plan_create(mrrr_plan** plan, const mrrr_options* opt) {
       o.vector_precision < 0 || o.vector_precision > 2 || o.singleton_rq < -1 || o.singleton_rq > 4)
     return MRRR_ERR_ARG;
   if (o.gap_tol >= 1.0 || o.classify_rtol >= 0.25 || o.threads_per_block % 32 != 0) return MRRR_ERR_ARG;
+  if (o.cluster_rtol >= 0.25 || o.prebisect_rtol >= 0.25 || !std::isfinite(o.root_perturb) ||
+      !std::isfinite(o.width_scale))
+    return MRRR_ERR_ARG;
   int dev = 0, nsm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return MRRR_ERR_CUDA;
   if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return MRRR_ERR_CUDA;

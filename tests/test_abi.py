@@ -49,6 +49,24 @@ def test_options_defaults(lib):
     assert lib.mrrr_options_default(None) == _lib.ERR_ARG
 
 
+@pytest.mark.parametrize("field,value", [
+    ("multisection_width", 3), ("multisection_width", 64), ("root_side", 3),
+    ("vector_precision", 3), ("singleton_rq", 5), ("singleton_rq", -2),
+    ("gap_tol", 1.5), ("gap_tol", float("inf")), ("classify_rtol", 0.5),
+    ("cluster_rtol", 0.25), ("cluster_rtol", float("inf")), ("prebisect_rtol", 0.5),
+    ("prebisect_rtol", float("inf")), ("root_perturb", float("inf")),
+    ("width_scale", float("inf")), ("threads_per_block", 48),
+])
+def test_plan_create_rejects_options_out_of_range(lib, field, value):
+    # the checks come before the first CUDA call, so they run without a GPU
+    o = _lib.Options()
+    assert lib.mrrr_options_default(ctypes.byref(o)) == 0
+    setattr(o, field, value)
+    plan = ctypes.c_void_p(0x1234)
+    assert lib.mrrr_plan_create(ctypes.byref(plan), ctypes.byref(o)) == _lib.ERR_ARG
+    assert plan.value is None  # NULL on failure
+
+
 def test_status_strings(lib):
     for code in range(9):
         s = lib.mrrr_status_string(code)
