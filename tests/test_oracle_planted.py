@@ -1,0 +1,176 @@
+"""The tridiagonal oracle's pins catch plausible mistakes in its C code
+(CPU only).
+
+Each case copies oracle/oracle.c, plants one mistake of the kind a careful
+reader could still make -- a flipped sign in the Sturm recurrence, an index
+off by one, a dropped term of the banded LU, a skipped Gram-Schmidt pass, a
+wrong split row, a Jacobi rotation with the wrong angle -- compiles the copy
+with the oracle's own flags and runs a battery of the pins against it in a
+child process (so that a mistake that crashes the copy cannot take the test
+run down).  The battery holds only checks fixed outside the oracle: the 1-2-1
+Toeplitz and Clement closed forms, LAPACK's tridiagonal eigenvalues, residual
+and orthogonality against the accuracy goals (paper Sec. 2.3, Eqs. Tresnorm
+and Torthogo), Sturm counts between LAPACK's separated eigenvalues, and
+subspaces of LAPACK's eigenvectors.  The unchanged copy must pass every
+check; every planted mistake must fail at least one.
+"""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "oracle.c")
+EPS = 2.0 ** -53
+
+# (name, text in oracle.c, replacement): each text occurs exactly once
+MISTAKES = [
+    ("sturm recurrence sign", "q = (d[i] - x) - e2[i - 1] / q;", "q = (d[i] - x) + e2[i - 1] / q;"),
+    ("sturm first pivot sign", "double q = d[0] - x;", "double q = x - d[0];"),
+    ("block bisection index off by one",
+     "if (sturm_count_block(b->m, b->d, b->e2, mid, b->pivmin) >= k)",
+     "if (sturm_count_block(b->m, b->d, b->e2, mid, b->pivmin) > k)"),
+    ("k-th eigenvalue index off by one", "if (cnt >= k)", "if (cnt > k)"),
+    ("sturm count of a split T keeps only the last block",
+     "total += sturm_count_block(m, d + s, blk.e2, x, blk.pivmin);",
+     "total = sturm_count_block(m, d + s, blk.e2, x, blk.pivmin);"),
+    ("split block starts one row early", "starts[nb++] = i + 1;", "starts[nb++] = i;"),
+    ("blocks' eigenvalues not merged in order", "    qsort(all, nitems, sizeof(eig_t), eig_cmp);\n", ""),
+    ("LU elimination sign", "w0 = a1 - mk * w1;", "w0 = a1 + mk * w1;"),
+    ("LU back substitution drops the second superdiagonal",
+     "    if (k + 2 < m) v -= f->u2[k] * x[k + 2];\n", ""),
+    ("inverse iteration shift sign", "lu_factor(&f, d, es, mu, tiny);", "lu_factor(&f, d, es, -mu, tiny);"),
+    ("Gram-Schmidt adds the projection", "for (int i = 0; i < m; ++i) x[i] -= h * v[i];",
+     "for (int i = 0; i < m; ++i) x[i] += h * v[i];"),
+    ("no Gram-Schmidt inside clusters", "for (int pass = 0; pass < 2; ++pass)", "for (int pass = 0; pass < 0; ++pass)"),
+    ("cluster rule inverted", "q->value - p->value <= orfac * bnorm[q->block]",
+     "q->value - p->value > orfac * bnorm[q->block]"),
+    ("vectors not normalised", "for (int i = 0; i < m; ++i) out[i] = x[i] / nx;",
+     "for (int i = 0; i < m; ++i) out[i] = x[i];"),
+    ("Jacobi angle sign", "double theta = (aqq - app) / (2.0 * apq);", "double theta = (app - aqq) / (2.0 * apq);"),
+    ("Jacobi rotation of V", "V[q * n + k] = s * vkp + c * vkq;", "V[q * n + k] = s * vkp - c * vkq;"),
+]
+
+
+def run_battery(lib_path):
+    """The pins, run on the oracle library at lib_path; returns the names of
+    the checks that failed (NaN fails every comparison)."""
+    import numpy as np
+    import scipy.linalg
+
+    import oracle.oracle as om
+    from paper_1205_2107_gb300 import inputs
+
+    om.build = lambda force=False: lib_path
+    om._lib = None
+    failed = []
+
+    def check(name, ok):
+        if not bool(ok):
+            failed.append(name)
+
+    def pairs(name, d, e, il=None, iu=None):
+        n = len(d)
+        ref = scipy.linalg.eigvalsh_tridiagonal(d, e)
+        tn = float(np.max(np.abs(ref)))
+        W, Z = om.eigh_tridiagonal(d, e, il, iu)
+        lo, hi = (0, n) if il is None else (il - 1, iu)
+        check(name + " values (LAPACK)",
+              W.shape == (hi - lo,) and np.max(np.abs(W - ref[lo:hi])) <= 4 * n * EPS * tn)
+        R = om.tridiag_dense(d, e) @ Z - Z * W[None, :]
+        check(name + " residual", np.max(np.linalg.norm(R, axis=0)) <= 20 * n * EPS * tn)
+        check(name + " orthogonality", np.max(np.abs(Z.T @ Z - np.eye(Z.shape[1]))) <= 20 * n * EPS)
+
+    # 1-2-1 Toeplitz: eigenvalues and sine eigenvectors in closed form
+    n = 64
+    d, e = inputs.toeplitz(n)
+    lam = inputs.toeplitz_eigenvalues(n)
+    W, Z = om.eigh_tridiagonal(d, e)
+    check("toeplitz values", np.max(np.abs(W - lam)) <= 4 * n * EPS * np.max(np.abs(lam)))
+    j = np.arange(1, n + 1)
+    k = np.arange(1, n + 1)
+    S = np.sin(np.outer(j, k) * np.pi / (n + 1))
+    S = S[:, np.argsort(2.0 - 2.0 * np.cos(k * np.pi / (n + 1)))]
+    S /= np.linalg.norm(S, axis=0)
+    check("toeplitz vectors", np.min(np.abs(np.sum(S * Z, axis=0))) >= 1.0 - 1e-10)
+    # Clement: integer spectrum
+    n = 51
+    d, e = inputs.clement(n)
+    check("clement values", np.max(np.abs(om.eigvalsh_tridiagonal(d, e) - inputs.clement_eigenvalues(n)))
+          <= 4 * n * EPS * (n - 1))
+    # LAPACK, residual and orthogonality: random, Wilkinson pairs, glued groups
+    pairs("uniform", *inputs.uniform(200, 7))
+    pairs("wilkinson W+ 201", *inputs.wilkinson_plus(201))
+    pairs("glued W21+ x20", *inputs.glued_wilkinson(20))
+    # a T that splits in three blocks: all, a subset, counts, single eigenvalues
+    d, e = inputs.uniform(120, 9)
+    e = e.copy()
+    e[39] = 0.0
+    e[84] = 0.0
+    pairs("split", d, e)
+    pairs("split subset", d, e, 30, 70)
+    ref = scipy.linalg.eigvalsh_tridiagonal(d, e)
+    tn = float(np.max(np.abs(ref)))
+    sep = [i for i in range(0, 119, 5) if ref[i + 1] - ref[i] > 1e-8]
+    check("sturm counts (split)", all(om.sturm_count(d, e, 0.5 * (ref[i] + ref[i + 1])) == i + 1 for i in sep))
+    check("k-th eigenvalue (split)",
+          all(abs(om.kth_eigenvalue(d, e, kk) - ref[kk - 1]) <= 4 * 120 * EPS * tn for kk in (1, 17, 60, 120)))
+    # one cluster's vectors: the subspace of W+'s largest pair
+    d, e = inputs.wilkinson_plus(201)
+    wref, zref = scipy.linalg.eigh_tridiagonal(d, e, select="i", select_range=(199, 200))
+    Zc = om.cluster_vectors(d, e, wref)
+    sv = np.linalg.svd(zref.T @ Zc, compute_uv=False)
+    check("cluster vectors subspace", np.min(sv) >= 1.0 - 1e-10 and np.max(sv) <= 1.0 + 1e-10)
+    # Jacobi against LAPACK's dense solver
+    n = 17
+    d, e = inputs.uniform(n, 3)
+    T = om.tridiag_dense(d, e)
+    Wj, V = om.jacobi(d, e)
+    ref = np.linalg.eigvalsh(T)
+    tn = float(np.max(np.abs(ref)))
+    check("jacobi values", np.max(np.abs(Wj - ref)) <= 4 * n * EPS * tn)
+    check("jacobi vectors", np.max(np.linalg.norm(T @ V - V * Wj[None, :], axis=0)) <= 20 * n * EPS * tn
+          and np.max(np.abs(V.T @ V - np.eye(n))) <= 20 * n * EPS)
+    return failed
+
+
+def _compile(text, out):
+    src = out[:-3] + ".c"
+    with open(src, "w") as f:
+        f.write(text)
+    # the flags oracle.build uses
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread", "-ffp-contract=off",
+                    "-fno-fast-math", "-o", out, src, "-lm"], check=True)
+    return out
+
+
+def _battery_in_child(lib_path):
+    code = ("import json, sys; sys.path.insert(0, %r); "
+            "from tests.test_oracle_planted import run_battery; "
+            "print(json.dumps(run_battery(%r)))" % (ROOT, lib_path))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300, cwd=ROOT)
+    if r.returncode != 0:
+        return None, r.stderr[-2000:]
+    return json.loads(r.stdout.strip().splitlines()[-1]), ""
+
+
+def _source():
+    with open(SRC) as f:
+        return f.read()
+
+
+def test_unchanged_oracle_passes_the_battery(tmp_path):
+    failed, err = _battery_in_child(_compile(_source(), str(tmp_path / "liboracle_ok.so")))
+    assert failed == [], (failed, err)
+
+
+@pytest.mark.parametrize("name,old,new", MISTAKES, ids=[m[0] for m in MISTAKES])
+def test_planted_mistake_fails_a_pin(tmp_path, name, old, new):
+    text = _source()
+    assert text.count(old) == 1, "the planted text must occur exactly once in oracle.c"
+    lib = _compile(text.replace(old, new), str(tmp_path / "liboracle_planted.so"))
+    failed, err = _battery_in_child(lib)
+    # a copy that crashes has failed too; otherwise at least one pin must fail
+    assert failed is None or len(failed) > 0, name
