@@ -12,7 +12,9 @@ Toeplitz and Clement closed forms, LAPACK's tridiagonal eigenvalues, residual
 and orthogonality against the accuracy goals (paper Sec. 2.3, Eqs. Tresnorm
 and Torthogo), Sturm counts between LAPACK's separated eigenvalues, and
 subspaces of LAPACK's eigenvectors.  The unchanged copy must pass every
-check; every planted mistake must fail at least one.
+check; every planted mistake must fail at least one.  The same is done for
+the Python layer (oracle/oracle.py: the power-of-two scaling and the layout
+of the C library's results) on a copy of the whole oracle package.
 """
 import json
 import os
@@ -54,22 +56,27 @@ MISTAKES = [
 ]
 
 
-def run_battery(lib_path):
-    """The pins, run on the oracle library at lib_path; returns the names of
-    the checks that failed (NaN fails every comparison)."""
+def run_battery(lib_path=None):
+    """The pins, run on the oracle (its library replaced by lib_path when
+    given); returns the names of the checks that failed (NaN fails every
+    comparison)."""
     import numpy as np
     import scipy.linalg
 
     import oracle.oracle as om
     from paper_1205_2107_gb300 import inputs
 
-    om.build = lambda force=False: lib_path
-    om._lib = None
+    if lib_path is not None:
+        om.build = lambda force=False: lib_path
+        om._lib = None
     failed = []
 
     def check(name, ok):
         if not bool(ok):
             failed.append(name)
+
+    def dense(d, e):  # T from its definition, not through the oracle
+        return np.diag(d) + np.diag(e, 1) + np.diag(e, -1)
 
     def pairs(name, d, e, il=None, iu=None):
         n = len(d)
@@ -77,9 +84,11 @@ def run_battery(lib_path):
         tn = float(np.max(np.abs(ref)))
         W, Z = om.eigh_tridiagonal(d, e, il, iu)
         lo, hi = (0, n) if il is None else (il - 1, iu)
-        check(name + " values (LAPACK)",
-              W.shape == (hi - lo,) and np.max(np.abs(W - ref[lo:hi])) <= 4 * n * EPS * tn)
-        R = om.tridiag_dense(d, e) @ Z - Z * W[None, :]
+        check(name + " shapes", W.shape == (hi - lo,) and Z.shape == (n, hi - lo))
+        if W.shape != (hi - lo,) or Z.shape != (n, hi - lo):
+            return
+        check(name + " values (LAPACK)", np.max(np.abs(W - ref[lo:hi])) <= 4 * n * EPS * tn)
+        R = dense(d, e) @ Z - Z * W[None, :]
         check(name + " residual", np.max(np.linalg.norm(R, axis=0)) <= 20 * n * EPS * tn)
         check(name + " orthogonality", np.max(np.abs(Z.T @ Z - np.eye(Z.shape[1]))) <= 20 * n * EPS)
 
@@ -126,7 +135,7 @@ def run_battery(lib_path):
     # Jacobi against LAPACK's dense solver
     n = 17
     d, e = inputs.uniform(n, 3)
-    T = om.tridiag_dense(d, e)
+    T = dense(d, e)
     Wj, V = om.jacobi(d, e)
     ref = np.linalg.eigvalsh(T)
     tn = float(np.max(np.abs(ref)))
@@ -146,10 +155,13 @@ def _compile(text, out):
     return out
 
 
-def _battery_in_child(lib_path):
-    code = ("import json, sys; sys.path.insert(0, %r); "
+def _battery_in_child(lib_path=None, pkg_root=None):
+    """run_battery in a child process; with pkg_root, ``import oracle`` finds
+    the copy of the oracle package there."""
+    paths = [p for p in (pkg_root, ROOT) if p]
+    code = ("import json, sys; sys.path[:0] = %r; "
             "from tests.test_oracle_planted import run_battery; "
-            "print(json.dumps(run_battery(%r)))" % (ROOT, lib_path))
+            "print(json.dumps(run_battery(%r)))" % (paths, lib_path))
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300, cwd=ROOT)
     if r.returncode != 0:
         return None, r.stderr[-2000:]
@@ -174,3 +186,45 @@ def test_planted_mistake_fails_a_pin(tmp_path, name, old, new):
     failed, err = _battery_in_child(lib)
     # a copy that crashes has failed too; otherwise at least one pin must fail
     assert failed is None or len(failed) > 0, name
+
+
+# mistakes in the Python layer of the oracle (oracle/oracle.py): the power-of-
+# two scaling and the layout of what the C library returns
+PY_MISTAKES = [
+    ("eigenvalues not scaled back", "return np.ldexp(W[:k], -s), Zf[:k, :n].T.copy()",
+     "return np.ldexp(W[:k], s), Zf[:k, :n].T.copy()"),
+    ("Z returned transposed", "return np.ldexp(W[:k], -s), Zf[:k, :n].T.copy()",
+     "return np.ldexp(W[:k], -s), Zf[:k, :n].copy()"),
+    ("Sturm count at an unscaled x", "float(np.ldexp(float(x), k))", "float(x)"),
+    ("k-th eigenvalue not scaled back", "_load().oracle_kth_eigenvalue(n, _ptr(d), _ptr(eb), int(k)), -s)",
+     "_load().oracle_kth_eigenvalue(n, _ptr(d), _ptr(eb), int(k)), s)"),
+    ("cluster shifts not scaled", "mus = np.ldexp(_f64(mus), s)", "mus = _f64(mus)"),
+    ("Jacobi V returned transposed", "return np.ldexp(W, -s), V.T.copy()", "return np.ldexp(W, -s), V.copy()"),
+]
+
+
+def _package_copy(dst, old=None, new=None):
+    import shutil
+    pkg = os.path.join(dst, "oracle")
+    os.makedirs(pkg)
+    for name in ("__init__.py", "oracle.py", "oracle.c", "dense.py"):
+        shutil.copy(os.path.join(ROOT, "oracle", name), pkg)
+    if old is not None:
+        path = os.path.join(pkg, "oracle.py")
+        with open(path) as f:
+            text = f.read()
+        assert text.count(old) == 1, "the planted text must occur exactly once in oracle.py"
+        with open(path, "w") as f:
+            f.write(text.replace(old, new))
+    return dst
+
+
+def test_unchanged_oracle_package_passes_the_battery(tmp_path):
+    failed, err = _battery_in_child(pkg_root=_package_copy(str(tmp_path)))
+    assert failed == [], (failed, err)
+
+
+@pytest.mark.parametrize("name,old,new", PY_MISTAKES, ids=[m[0] for m in PY_MISTAKES])
+def test_planted_python_mistake_fails_a_pin(tmp_path, name, old, new):
+    failed, err = _battery_in_child(pkg_root=_package_copy(str(tmp_path), old, new))
+    assert failed, (name, err)  # the battery runs through and records a failed pin
