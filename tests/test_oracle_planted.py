@@ -14,7 +14,9 @@ and Torthogo), Sturm counts between LAPACK's separated eigenvalues, and
 subspaces of LAPACK's eigenvectors.  The unchanged copy must pass every
 check; every planted mistake must fail at least one.  The same is done for
 the Python layer (oracle/oracle.py: the power-of-two scaling and the layout
-of the C library's results) on a copy of the whole oracle package.
+of the C library's results) and for the dense stages (oracle/dense.py,
+against NumPy's and SciPy's LAPACK routines and the stages' defining
+identities) on a copy of the whole oracle package.
 """
 import json
 import os
@@ -155,13 +157,14 @@ def _compile(text, out):
     return out
 
 
-def _battery_in_child(lib_path=None, pkg_root=None):
-    """run_battery in a child process; with pkg_root, ``import oracle`` finds
-    the copy of the oracle package there."""
+def _battery_in_child(lib_path=None, pkg_root=None, battery="run_battery"):
+    """A battery (run_battery or run_dense_battery) in a child process; with
+    pkg_root, ``import oracle`` finds the copy of the oracle package there."""
     paths = [p for p in (pkg_root, ROOT) if p]
+    args = "%r" % (lib_path,) if battery == "run_battery" else ""
     code = ("import json, sys; sys.path[:0] = %r; "
-            "from tests.test_oracle_planted import run_battery; "
-            "print(json.dumps(run_battery(%r)))" % (paths, lib_path))
+            "from tests.test_oracle_planted import %s; "
+            "print(json.dumps(%s(%s)))" % (paths, battery, battery, args))
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300, cwd=ROOT)
     if r.returncode != 0:
         return None, r.stderr[-2000:]
@@ -203,17 +206,17 @@ PY_MISTAKES = [
 ]
 
 
-def _package_copy(dst, old=None, new=None):
+def _package_copy(dst, old=None, new=None, module="oracle.py"):
     import shutil
     pkg = os.path.join(dst, "oracle")
     os.makedirs(pkg)
     for name in ("__init__.py", "oracle.py", "oracle.c", "dense.py"):
         shutil.copy(os.path.join(ROOT, "oracle", name), pkg)
     if old is not None:
-        path = os.path.join(pkg, "oracle.py")
+        path = os.path.join(pkg, module)
         with open(path) as f:
             text = f.read()
-        assert text.count(old) == 1, "the planted text must occur exactly once in oracle.py"
+        assert text.count(old) == 1, "the planted text must occur exactly once in " + module
         with open(path, "w") as f:
             f.write(text.replace(old, new))
     return dst
@@ -228,3 +231,104 @@ def test_unchanged_oracle_package_passes_the_battery(tmp_path):
 def test_planted_python_mistake_fails_a_pin(tmp_path, name, old, new):
     failed, err = _battery_in_child(pkg_root=_package_copy(str(tmp_path), old, new))
     assert failed, (name, err)  # the battery runs through and records a failed pin
+
+
+def run_dense_battery():
+    """The dense oracle's pins (oracle/dense.py, paper Sec. 1.2 stages 1-6)
+    against NumPy's and SciPy's LAPACK routines and the defining identities;
+    returns the names of the checks that failed."""
+    import numpy as np
+    import scipy.linalg
+
+    from oracle import dense as od
+
+    failed = []
+
+    def check(name, ok):
+        if not bool(ok):
+            failed.append(name)
+
+    rng = np.random.default_rng(1205)
+    n = 40
+    X = rng.standard_normal((n, n))
+    A = (X + X.T) / 2
+    G = rng.standard_normal((n, n))
+    B = G @ G.T + n * np.eye(n)
+    an = float(np.linalg.norm(A, 2))
+    tol = 1e-12
+    # a reflector maps x onto beta e_1, with beta of the sign opposite to x_0
+    x = rng.standard_normal(7)
+    v, tau, beta = od.householder_vector(x)
+    H = np.eye(7) - tau * np.outer(v, v)
+    e1 = np.zeros(7)
+    e1[0] = 1.0
+    check("reflector maps onto e_1", v[0] == 1.0 and np.max(np.abs(H @ x - beta * e1)) <= tol * np.linalg.norm(x))
+    check("reflector sign", abs(beta + np.sign(x[0]) * np.linalg.norm(x)) <= tol * np.linalg.norm(x))
+    # stage 3: Q^T A Q = T with Q orthogonal, T's eigenvalues LAPACK's
+    d, e, V, tau = od.tridiagonal_reduction(A)
+    Q = od.form_q(V, tau, n)
+    T = np.diag(d) + np.diag(e, 1) + np.diag(e, -1)
+    ref = np.linalg.eigvalsh(A)
+    check("Q orthogonal", np.max(np.abs(Q.T @ Q - np.eye(n))) <= tol)
+    check("Q^T A Q = T", np.max(np.abs(Q.T @ A @ Q - T)) <= tol * an)
+    check("T's eigenvalues", np.max(np.abs(np.linalg.eigvalsh(T) - ref)) <= tol * an)
+    # stages 3-5: the standard problem
+    W, Y = od.eigh_dense(A)
+    check("dense eigenvalues", np.max(np.abs(W - ref)) <= tol * an)
+    check("dense residual", np.max(np.linalg.norm(A @ Y - Y * W[None, :], axis=0)) <= tol * an)
+    check("dense orthogonality", np.max(np.abs(Y.T @ Y - np.eye(n))) <= tol)
+    # stage 1 and the triangular solves
+    L = od.cholesky(B)
+    bn = float(np.linalg.norm(B, 2))
+    check("cholesky lower", np.all(np.triu(L, 1) == 0.0))
+    check("cholesky is numpy's", np.max(np.abs(L - np.linalg.cholesky(B))) <= tol * np.sqrt(bn))
+    R = rng.standard_normal((n, 3))
+    Lr = np.linalg.cholesky(B)
+    check("forward substitution", np.max(np.abs(Lr @ od.forward_substitution(Lr, R) - R)) <= tol * bn)
+    check("back substitution", np.max(np.abs(Lr.T @ od.back_substitution_transposed(Lr, R) - R)) <= tol * bn)
+    # stage 2: C = L^-1 A L^-T against SciPy's triangular solves
+    C = od.reduce_generalized(A, Lr)
+    M = scipy.linalg.solve_triangular(Lr, A, lower=True)
+    Cref = scipy.linalg.solve_triangular(Lr, M.T, lower=True)
+    check("reduction to standard form", np.max(np.abs(C - Cref)) <= tol * an)
+    # stages 1-6: the pencil
+    Wg, Xg = od.eigh_generalized(A, B)
+    wref = scipy.linalg.eigh(A, B, eigvals_only=True)
+    check("pencil eigenvalues", np.max(np.abs(Wg - wref)) <= tol * an)
+    check("A X = B X Lambda", np.max(np.abs(A @ Xg - (B @ Xg) * Wg[None, :])) <= tol * an)
+    check("X^T B X = I", np.max(np.abs(Xg.T @ B @ Xg - np.eye(n))) <= tol * n)
+    return failed
+
+
+# mistakes in the dense oracle (oracle/dense.py)
+DENSE_MISTAKES = [
+    ("reflector sign that cancels", "beta = -norm if alpha >= 0.0 else norm", "beta = norm if alpha >= 0.0 else -norm"),
+    ("reflector factor sign", "tau = (beta - alpha) / beta", "tau = (alpha - beta) / beta"),
+    ("two-sided update without its correction", "w = p - (0.5 * t * float(p @ v)) * v", "w = p"),
+    ("reflectors applied first to last", "for k in range(V.shape[1] - 1, -1, -1):", "for k in range(V.shape[1]):"),
+    ("stage 5 left out", "return W, apply_q(V, tau, Z)", "return W, Z"),
+    ("Cholesky pivot without the earlier columns", "s = B[j, j] - float(L[j, :j] @ L[j, :j])", "s = B[j, j]"),
+    ("Cholesky column divided by the pivot squared",
+     "L[j + 1:, j] = (B[j + 1:, j] - L[j + 1:, :j] @ L[j, :j]) / L[j, j]",
+     "L[j + 1:, j] = (B[j + 1:, j] - L[j + 1:, :j] @ L[j, :j]) / s"),
+    ("forward substitution without the division", "X[i] = (X[i] - L[i, :i] @ X[:i]) / L[i, i]",
+     "X[i] = X[i] - L[i, :i] @ X[:i]"),
+    ("back substitution by rows of L instead of columns", "X[i] = (X[i] - L[i + 1:, i] @ X[i + 1:]) / L[i, i]",
+     "X[i] = (X[i] - L[i, i + 1:] @ X[i + 1:]) / L[i, i]"),
+    ("second solve of stage 2 without the transpose", "C = forward_substitution(L, M.T)",
+     "C = forward_substitution(L, M)"),
+    ("stage 6 by L^-1 instead of L^-T", "return W, back_substitution_transposed(L, Y)",
+     "return W, forward_substitution(L, Y)"),
+]
+
+
+def test_unchanged_dense_oracle_passes_the_battery(tmp_path):
+    failed, err = _battery_in_child(pkg_root=_package_copy(str(tmp_path)), battery="run_dense_battery")
+    assert failed == [], (failed, err)
+
+
+@pytest.mark.parametrize("name,old,new", DENSE_MISTAKES, ids=[m[0] for m in DENSE_MISTAKES])
+def test_planted_dense_mistake_fails_a_pin(tmp_path, name, old, new):
+    failed, err = _battery_in_child(pkg_root=_package_copy(str(tmp_path), old, new, module="dense.py"),
+                                    battery="run_dense_battery")
+    assert failed, (name, err)
