@@ -43,7 +43,9 @@ class Plan:
     Options are the fields of ``mrrr_options`` (gap_tol, classify_rtol,
     max_depth, max_bisect_steps, engine_blocks_per_sm, threads_per_block,
     vec_blocks_per_sm, use_graph, max_nodes, pool_rows, cluster_rtol,
-    root_perturb, width_scale); zero or absent means default.  With
+    root_perturb, width_scale, prebisect_rtol, multisection_width, root_side,
+    vector_precision, singleton_rq); zero or absent means default, and a
+    value out of range raises (MRRR_ERR_ARG) when the plan is created.  With
     ``use_graph=1`` a solve is captured once per call signature into a CUDA
     graph and replayed.
     """
