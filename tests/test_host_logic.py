@@ -75,6 +75,34 @@ def test_bench_records_the_host_cpu():
     assert h["nproc"] == os.cpu_count() and h["nproc"] >= 1
 
 
+def test_reference_arm_prints_one_contract_line(monkeypatch, capsys):
+    """bench.py --impl reference: rank 0 prints one JSON line that carries the
+    metric, the oracle sample as cpu_baseline, and an e2e with no copies;
+    another rank prints nothing.  The window calibration is stubbed to one
+    window per matrix, and the matrices to small ones, to keep this quick."""
+    import argparse
+    import json
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setattr(bench, "workload_matrices",
+                        lambda: [("a", *inputs.wilkinson_plus(301)), ("b", *inputs.glued_wilkinson(10))])
+    monkeypatch.setattr(bench, "calibrated_windows", lambda mats, cores, secs: 1)
+    args = argparse.Namespace(steps=2, warmup=1)
+    bench.run_reference(args, rank=1, world=2)
+    assert capsys.readouterr().out == ""
+    bench.run_reference(args, rank=0, world=1)
+    lines = [ln for ln in capsys.readouterr().out.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == bench.UNIT
+    assert line["steps"] == 2 and line["warmup"] == 1 and line["higher_is_better"] is True
+    assert line["value"] > 0 and line["cpu_baseline"]["value"] == line["value"]
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"] == {"value": line["value"], "unit": bench.UNIT, "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+    assert line["config"]["workload"] == bench.WORKLOAD
+
+
 class _FakePlan:
     """Stands in for api.Plan in the retry loop: records option changes and
     reports the scripted statuses one solve after another."""
