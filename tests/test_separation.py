@@ -111,6 +111,29 @@ def test_public_calls_refuse_cpu_tensors():
         api.eigh_tridiagonal(np.zeros(8), np.zeros(7))
 
 
+def test_dense_slice_and_shard_calls_refuse_cpu_tensors():
+    """The same for the dense stages, the index slices and the sharded
+    driver."""
+    from paper_1205_2107_gb300 import shard
+    A, d = torch.eye(4, dtype=torch.float64), _cpu(8)
+    calls = [lambda: api.tridiagonalize(A), lambda: api.apply_q(A, _cpu(2), A), lambda: api.eigh_dense(A),
+             lambda: api.eigh_dense(A, 1, 2, vectors=False), lambda: api.cholesky(A),
+             lambda: api.eigh_generalized(A, A), lambda: api.eigh_tridiagonal_slice(d, d, None, None, 2, 0),
+             lambda: shard.eigh_tridiagonal_sharded(d, d)]
+    for call in calls:
+        with pytest.raises(TypeError, match="CUDA tensor"):
+            call()
+
+
+def test_a_missing_library_raises(monkeypatch):
+    """Without libmrrr.so the binding raises; nothing else computes."""
+    from paper_1205_2107_gb300 import _lib
+    monkeypatch.setattr(_lib, "_lib", None)
+    monkeypatch.setattr(_lib._build, "LIB", os.path.join(ROOT, "no_such_dir", "libmrrr.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        _lib.load()
+
+
 def test_empty_problem_still_needs_a_device_tensor():
     with pytest.raises(TypeError, match="CUDA tensor"):
         api.eigh_tridiagonal(_cpu(0), _cpu(0))
